@@ -1,0 +1,389 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the mixed-radix gate-apply engine.
+
+Workload (one GPU): 14 qutrits (3^14 = 4,782,969 amplitudes), a seeded
+500-gate circuit (40% Haar single-qutrit, 30% F_3, 30% controlled-X_3 on random
+pairs and control levels), per-gate kernels.  One step = reset the register to
+|0...0>, run the circuit, write the FP64 probabilities of all amplitudes to a
+device buffer.  The headline runs the complex64 (FP32) path; the complex128
+(FP64) path is measured in the same run for comparison.
+
+Prints one JSON line (see the repository's design notes for every key).
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank runs an independent replica on its own GPU; rank 0
+prints the line with the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "gates/s & amplitude updates/s vs HBM roofline, fused FP32 vs plain FP64, fid>=1-1e-6"
+UNIT = "gates/s"
+WORKLOAD = "14 qutrits (3^14 = 4,782,969 amplitudes), 500-gate random circuit (40% Haar-1, 30% F_3, 30% CX_3), per-gate kernels"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-sample-gates", type=int, default=0, help="gates in the CPU-baseline sample (0: auto)")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------ helpers
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2211_07918_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(f.encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kname: str):
+    """dram bytes per launch for kernel class ``kname`` from a committed ncu
+    summary in profiles/, or None if absent or taken on different sources."""
+    pdir = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(pdir):
+        return None
+    sha = kernel_source_sha()
+    for f in sorted(os.listdir(pdir)):
+        if not f.endswith(".md"):
+            continue
+        with open(os.path.join(pdir, f)) as fh:
+            txt = fh.read()
+        m = re.search(r"^traffic_kernel_class:\s*(\S+)", txt, re.M)
+        t = re.search(r"^traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt, re.M)
+        s = re.search(r"^source_sha:\s*(\S+)", txt, re.M)
+        if m and t and s and m.group(1) == kname and s.group(1) == sha:
+            return float(t.group(1))
+    return None
+
+
+# ------------------------------------------------------------- CPU baseline
+
+def cpu_sample(dims, gates, ngates_sample):
+    """Time the FP64 C oracle (index loop, OpenMP over all host cores) on the
+    first ``ngates_sample`` gates of the circuit on the full register."""
+    from oracle import fast as qf
+    from oracle import qudit_oracle as qo
+    qf.build()
+    psi = qo.basis_state(dims)
+    sub = gates[:ngates_sample]
+    t0 = time.perf_counter()
+    for g in sub:
+        qf.apply(psi, dims, g)
+    dt = time.perf_counter() - t0
+    return len(sub) / dt, qf.max_threads(), dt
+
+
+def cpu_baseline_obj(dims, gates, ngates):
+    n = ngates or len(gates)
+    rate, cores, dt = cpu_sample(dims, gates, n)
+    return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {n} of {len(gates)} gates on the full 3^14 register, FP64 C index loop "
+                      f"(OpenMP), {dt:.1f} s"}
+
+
+# --------------------------------------------------------------- reference
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    from paper_2211_07918_gb300 import workloads as wl
+    dims, gates = wl.circuit_c1()
+    n = args.cpu_sample_gates or 100
+    for _ in range(args.warmup):
+        cpu_sample(dims, gates, 1)
+    rates, cores, secs = [], 0, 0.0
+    for _ in range(args.steps):
+        r, cores, dt = cpu_sample(dims, gates, n)
+        rates.append(r)
+        secs += dt
+    value = float(len(rates) * n / secs)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD + "; each step times a bounded sample of the circuit",
+                       "sample_gates_per_step": n},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"first {n} gates of the 500-gate circuit per step, full register"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# -------------------------------------------------------------------- ours
+
+def run_ours(args, rank, world, local):
+    import torch
+
+    from paper_2211_07918_gb300 import qudit as L
+    from paper_2211_07918_gb300 import workloads as wl
+    from paper_2211_07918_gb300.build import build
+
+    build()
+    L.load()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+
+    def barrier():
+        if pg is not None:
+            pg.barrier()
+        torch.cuda.synchronize()
+
+    dims, gates = wl.circuit_c1()
+    N = int(np.prod(dims))
+    ngates = len(gates)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    probs = torch.empty(N, dtype=torch.float64, device=dev)
+
+    def measure(prec, steps, warmup, profile):
+        reg = L.qd_create(dims, None, prec, 0, 0, stream.cuda_stream)
+        plan = L.qd_plan_create(reg, gates, L.QD_PLAN_NONE)
+        launches = L.qd_plan_info(plan)["launches"]
+        if profile:
+            L.qd_plan_profile(plan, True)
+
+        def step():
+            L.qd_reset(reg)
+            L.qd_plan_run(plan)
+            L.qd_probabilities(reg, where=L.QD_DEVICE, dev_ptr=probs.data_ptr())
+
+        for _ in range(warmup):
+            step()
+        barrier()
+        stream.synchronize()
+        per_step, kern = [], {}
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for i in range(steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()  # L2 flush outside the timed interval
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+            if profile:
+                ms, ab, kc = L.qd_plan_timings(plan)
+                for t, b, c in zip(ms, ab, kc):
+                    k = kern.setdefault(int(c), [0.0, 0.0, 0])
+                    k[0] += float(t)
+                    k[1] += float(b)
+                    k[2] += 1
+        stream.synchronize()
+        barrier()
+        per_step = [a.elapsed_time(b) for a, b in ev]
+        L.qd_plan_destroy(plan)
+        L.qd_destroy(reg)
+        return per_step, kern, launches
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    t_wall = time.perf_counter()
+    ms64, kern64, launches = measure(L.QD_C64, args.steps, args.warmup, True)
+    wall = time.perf_counter() - t_wall
+    clocks = sampler.stop()
+    ms128, kern128, _ = measure(L.QD_C128, max(3, args.steps // 4), args.warmup, False)
+
+    total_ms = float(sum(ms64))
+    if pg is not None:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_step = total_ms / args.steps
+    value = world * ngates / (ms_step * 1e-3)
+    ms_step128 = float(np.mean(ms128))
+
+    # dominant kernel class of the c64 path, measured with per-launch events
+    kname, kdata = None, None
+    for c, v in kern64.items():
+        if kdata is None or v[0] > kdata[0]:
+            kname, kdata = L.kclass_name(c), v
+    peak, peak_src = measured_peaks()
+    achieved = (kdata[1] / (kdata[0] * 1e-3)) / 1e9 if kdata else None
+    total_kernel_ms = sum(v[0] for v in kern64.values())
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None,
+                "traffic": profiled_traffic(kname),
+                "kernel": kname, "peak_source": peak_src,
+                "share_of_gate_time": kdata[0] / total_kernel_ms if kdata else None,
+                "launches": kdata[2] if kdata else 0,
+                "note": "state (38 MB c64) is L2-resident across the gates of a step; achieved can exceed HBM peak"}
+    all_bytes = sum(v[1] for v in kern64.values())
+
+    # e2e: host buffers through the public API: every step copies the initial
+    # state in from pinned host memory, replays the prepared circuit and reads
+    # all FP64 probabilities back to pinned host memory
+    host_in = torch.zeros(N, dtype=torch.complex64).pin_memory()
+    host_in[0] = 1.0
+    host_out = torch.empty(N, dtype=torch.float64).pin_memory()
+    hin = host_in.numpy()
+    hout = host_out.numpy()
+    reg = L.qd_create(dims, None, L.QD_C64, 0, 0, stream.cuda_stream)
+    plan = L.qd_plan_create(reg, gates, L.QD_PLAN_NONE)
+    for _ in range(2):
+        L.qd_set_amplitudes(reg, hin)
+        L.qd_plan_run(plan)
+        L.qd_probabilities(reg, hout)
+    e2e_steps = max(3, args.steps // 4)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        L.qd_set_amplitudes(reg, hin)
+        L.qd_plan_run(plan)
+        L.qd_probabilities(reg, hout)
+    stream.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    L.qd_plan_destroy(plan)
+    L.qd_destroy(reg)
+    e2e = {"value": world * ngates / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(N * 8),
+           "d2h_bytes_per_step": int(N * 8), "ms_per_step": e2e_s * 1e3,
+           "path": "qd_set_amplitudes(host) + qd_plan_run + qd_probabilities(host)"}
+
+    # fidelity of the timed c64 path against the c128 path on this GPU
+    regA = L.qd_create(dims, None, L.QD_C64, 0, 0, stream.cuda_stream)
+    regB = L.qd_create(dims, None, L.QD_C128, 0, 0, stream.cuda_stream)
+    L.qd_run_circuit(regA, gates)
+    L.qd_run_circuit(regB, gates)
+    a = L.qd_get_amplitudes(regA).astype(np.complex128)
+    b = L.qd_get_amplitudes(regB)
+    L.qd_destroy(regA)
+    L.qd_destroy(regB)
+    fid = float(abs(np.vdot(b, a)) ** 2)
+    maxabs = float(np.max(np.abs(a - b)))
+
+    cpu = None
+    if rank == 0 and world == 1:
+        cpu = cpu_baseline_obj(dims, gates, args.cpu_sample_gates)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "amplitudes": N, "gates": ngates, "precision": "complex64",
+                       "step": "reset + 500 gates + FP64 probabilities to device",
+                       "l2": "flushed (256 MiB write) before every timed step; inputs smaller than L2",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "amp_updates_per_s": value * N,
+            "alg_bytes_per_step": all_bytes / max(1, args.steps),
+            "compare": {"complex128_gates_per_s": world * ngates / (ms_step128 * 1e-3),
+                        "complex128_ms_per_step": ms_step128,
+                        "c64_over_c128": ms_step128 / ms_step,
+                        "c64_fidelity_vs_c128": fid, "c64_maxabs_vs_c128": maxabs},
+            "roofline": roofline,
+            "clocks": clocks,
+            "e2e": e2e,
+            "gpu_launches": int(args.steps * (launches + 2)),
+            "cpu_baseline": cpu,
+            "wall_s_timed_c64": wall,
+        }
+        print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.barrier()
+        pg.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,217 @@
+/*
+ * qudit.h - C ABI of libqudit, a GB300 (sm_103a) engine that applies
+ * generalized qudit gates in place to a mixed-radix state vector.
+ *
+ * The calls follow the problem statement of QuDiet (arXiv 2211.07918):
+ *   - a register is a heterogeneous list of qudit dimensions whose state has
+ *     N = prod d_q entries (Sec. 2.2); the first qudit is the least
+ *     significant digit (Sec. 3.2, qregs), so amplitude i is the basis state
+ *     with digits x_q = (i / s_q) mod d_q, s_q = prod_{p<q} d_p;
+ *   - each qudit starts in a chosen computational basis level, |0> by default
+ *     (Sec. 3.2, init_states);
+ *   - gates (Sec. 2.1.2 and Sec. 3.4): generalized NOT X^d_{+a}, phase shift
+ *     Z_d, generalized Hadamard F_d, generalized CNOT / multi-controlled
+ *     Toffoli that fire on a control level (d_c - 1 in the paper; any chosen
+ *     level here, after Fig. 1), and user-defined k-qudit matrices;
+ *   - the result is read as amplitudes or probabilities of the basis states
+ *     (Sec. 3.8, OutputMethod).
+ *
+ * Conventions for every call
+ *   - Return value: QD_OK (0) or a negative QD_ERR_* code.  No call aborts the
+ *     process or traps the GPU.  qd_last_error() gives a message for the
+ *     calling thread's most recent failure.
+ *   - Ownership: the caller owns every pointer it passes (dims, matrices,
+ *     target lists, output buffers); the library copies what it keeps.  A
+ *     device buffer given to qd_create stays owned by the caller (for example
+ *     torch storage) and must outlive the register.
+ *   - Streams: a stream argument is a cudaStream_t passed as void* (NULL is
+ *     the legacy default stream).  All device work of a register is ordered
+ *     on its stream; calls that return host values synchronise that stream.
+ *   - Gate matrices are host arrays of complex128 values stored as
+ *     interleaved (re, im) doubles, row-major D x D, D = prod of the target
+ *     dimensions.  The local index of a multi-qudit gate takes the
+ *     first-listed target as its most significant digit.  Matrices are
+ *     rounded to the register precision on the host.
+ *   - Amplitude buffers are complex64 (interleaved float) or complex128
+ *     (interleaved double) in the flat index order above.
+ */
+#ifndef QUDIT_H
+#define QUDIT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------ */
+#define QD_OK 0
+#define QD_ERR_ARG (-1)         /* null pointer, bad count, bad enum, bad shift or level */
+#define QD_ERR_DIM (-2)         /* dimension outside [2, 64], N above the limit, D too large */
+#define QD_ERR_OVERLAP (-3)     /* repeated target, or a control that is also a target */
+#define QD_ERR_OOM (-4)         /* device allocation failed or caller buffer too small */
+#define QD_ERR_CUDA (-5)        /* a CUDA runtime call failed */
+#define QD_ERR_TIMEOUT (-6)     /* a bounded device wait expired */
+#define QD_ERR_DEVICE (-7)      /* a kernel reported an error through the device error word */
+#define QD_ERR_UNSUPPORTED (-8) /* valid request this build does not implement */
+
+/* ---- enums ------------------------------------------------------------ */
+#define QD_C64 1  /* complex64 state: FP32 arithmetic */
+#define QD_C128 2 /* complex128 state: FP64 arithmetic */
+
+#define QD_HOST 0   /* output/input pointer is host memory */
+#define QD_DEVICE 1 /* output/input pointer is device memory */
+
+#define QD_GATE_X 1    /* X^d_{+a}: |x> -> |(x+a) mod d>, a = param in [1, d-1] (Sec. 2.1.2) */
+#define QD_GATE_Z 2    /* Z_d^p = diag(w^{p j}), w = exp(2 pi i/d), p = param (Sec. 2.1.2) */
+#define QD_GATE_H 3    /* F_d[j][k] = w^{jk}/sqrt(d) (Sec. 2.1.2) */
+#define QD_GATE_U 4    /* dense user matrix, D x D (Sec. 3.4 User Defined Gate) */
+#define QD_GATE_DIAG 5 /* diagonal user matrix, D entries */
+
+#define QD_PLAN_NONE 0       /* one kernel per gate, no fusion */
+#define QD_PLAN_GREEDY 1     /* greedy gate fusion into blocks */
+#define QD_PLAN_LEARNED 2    /* fusion steered by the learned cost model */
+#define QD_PLAN_EXHAUSTIVE 3 /* exact optimum over contiguous segmentations (small circuits) */
+
+#define QD_MAX_QUDITS 48
+#define QD_MAX_TARGETS 6
+#define QD_MAX_CONTROLS 8
+#define QD_MAX_D 32          /* largest target-space dimension of one per-gate kernel */
+#define QD_MAX_AMPLITUDES (((int64_t)1) << 40)
+
+/* One gate of a circuit.  Controls fire when every control qudit holds its
+ * level; a level of -1 means d_c - 1 (the paper's C_{X,d} and C^n_{X,d}). */
+typedef struct qd_gate {
+    int32_t kind;                          /* QD_GATE_* */
+    int32_t k;                             /* number of targets, 1..QD_MAX_TARGETS */
+    int32_t targets[QD_MAX_TARGETS];       /* first listed = most significant local digit */
+    int32_t nc;                            /* number of controls, 0..QD_MAX_CONTROLS */
+    int32_t controls[QD_MAX_CONTROLS];
+    int32_t ctrl_levels[QD_MAX_CONTROLS];  /* level in [0, d_c) or -1 */
+    int32_t param;                         /* X: shift a; Z: power p; otherwise ignored */
+    int32_t reserved;
+    const double *matrix;                  /* U: 2*D*D doubles; DIAG: 2*D doubles; else NULL */
+} qd_gate;
+
+typedef struct qd_reg qd_reg;   /* opaque register handle */
+typedef struct qd_plan qd_plan; /* opaque prepared circuit */
+
+/* ---- register (Sec. 2.2, Sec. 3.2, Sec. 3.3) --------------------------- */
+
+/* Create a register of n qudits with dims[q] in [2, 64] and
+ * N = prod dims[q] <= QD_MAX_AMPLITUDES, initialised to the basis state
+ * |init_levels[0] ... init_levels[n-1]> (NULL: all 0).
+ * precision: QD_C64 or QD_C128.  dev_buf: NULL to let the library allocate
+ * the N amplitudes, or a caller-owned device buffer of dev_buf_bytes >= N *
+ * element size, aligned to 16 bytes.  stream: cudaStream_t as void*.
+ * Errors: QD_ERR_ARG, QD_ERR_DIM, QD_ERR_OOM, QD_ERR_CUDA. */
+int qd_create(const int32_t *dims, int32_t n, const int32_t *init_levels, int32_t precision,
+              void *dev_buf, size_t dev_buf_bytes, void *stream, qd_reg **out);
+
+/* Release the register and everything the library allocated for it. */
+int qd_destroy(qd_reg *reg);
+
+/* Re-initialise to a basis state (NULL: all 0): one memset-class pass. */
+int qd_reset(qd_reg *reg, const int32_t *init_levels);
+
+/* Register facts: amplitude count, qudit count, device pointer of the state,
+ * precision.  Any output pointer may be NULL. */
+int qd_info(const qd_reg *reg, int64_t *num_amplitudes, int32_t *n, void **state, int32_t *precision);
+
+/* Move subsequent work of the register to another stream. */
+int qd_set_stream(qd_reg *reg, void *stream);
+
+/* ---- gate application, in place (Sec. 2.1.2, Sec. 3.4) ---------------- */
+
+/* Apply a dense D x D matrix to targets[0..k) under controls[0..nc) at
+ * ctrl_levels (NULL or -1 entries: d_c - 1).  The matrix is classified on
+ * the host: a diagonal or a permutation-with-phases matrix runs the
+ * data-movement kernels, anything else the dense kernels.  No check of
+ * unitarity.  Errors: QD_ERR_ARG, QD_ERR_DIM (D > QD_MAX_D), QD_ERR_OVERLAP. */
+int qd_apply(qd_reg *reg, const double *matrix, const int32_t *targets, int32_t k,
+             const int32_t *controls, const int32_t *ctrl_levels, int32_t nc);
+
+/* Apply a diagonal matrix given by its D complex entries. */
+int qd_apply_diag(qd_reg *reg, const double *diag, const int32_t *targets, int32_t k,
+                  const int32_t *controls, const int32_t *ctrl_levels, int32_t nc);
+
+/* X^d_{+shift} on t, shift in [1, d_t - 1] (Sec. 2.1.2 generalized NOT). */
+int qd_apply_x(qd_reg *reg, int32_t t, int32_t shift);
+/* Z_d^power on t (Sec. 2.1.2 phase shift; power is reduced mod d). */
+int qd_apply_z(qd_reg *reg, int32_t t, int32_t power);
+/* F_d on t (Sec. 2.1.2 generalized Hadamard). */
+int qd_apply_h(qd_reg *reg, int32_t t);
+/* C_{X,d}: X^{d_t}_{+shift} on t when control c holds ctrl_level
+ * (-1: d_c - 1) (Sec. 2.1.2 generalized CNOT; Sec. 3.4 cx((c,t), plus)). */
+int qd_apply_cx(qd_reg *reg, int32_t c, int32_t t, int32_t shift, int32_t ctrl_level);
+/* C^n_{X,d}: X_{+shift} on t when every control holds its level (NULL or -1:
+ * d_c - 1) (Sec. 2.1.2 multi-controlled Toffoli). */
+int qd_apply_mct(qd_reg *reg, const int32_t *controls, const int32_t *ctrl_levels, int32_t nc,
+                 int32_t t, int32_t shift);
+/* Apply one gate record. */
+int qd_apply_gate(qd_reg *reg, const qd_gate *gate);
+
+/* ---- circuits ---------------------------------------------------------- */
+
+/* Validate and prepare a gate list for repeated runs on this register:
+ * kernel choice, launch parameters and (plan_kind != QD_PLAN_NONE) gate
+ * fusion.  The gates array and its matrices may be freed after the call. */
+int qd_plan_create(qd_reg *reg, const qd_gate *gates, int32_t ngates, int32_t plan_kind, qd_plan **out);
+/* Enqueue the prepared circuit on the register's stream.  On a non-default
+ * stream the first run captures the launches into a CUDA graph and later runs
+ * replay it (one launch call per run); on the legacy default stream every run
+ * launches the kernels directly. */
+int qd_plan_run(qd_plan *plan);
+/* Number of kernel launches one run enqueues, and of fused blocks. */
+int qd_plan_info(const qd_plan *plan, int32_t *launches, int32_t *blocks);
+int qd_plan_destroy(qd_plan *plan);
+/* Per-launch timing: with enable != 0 every qd_plan_run records a CUDA
+ * event before each launch and after the last one on the register's stream.
+ * qd_plan_timings then synchronises the stream and writes, for launch i of
+ * the latest run, its device time in ms (events), its algorithmic HBM bytes
+ * (2 x bytes of the amplitudes it reads and writes) and its kernel class
+ * (QD_KCLASS_* | D << 8).  Any output pointer may be NULL. */
+#define QD_KCLASS_DENSE_DIRECT 0
+#define QD_KCLASS_DENSE_TILE 1
+#define QD_KCLASS_MONO_DIRECT 2
+#define QD_KCLASS_MONO_TILE 3
+int qd_plan_profile(qd_plan *plan, int32_t enable);
+int qd_plan_timings(qd_plan *plan, float *ms, double *alg_bytes, int32_t *kclass);
+/* Plan, run once with direct launches (no graph capture) and release. */
+int qd_run_circuit(qd_reg *reg, const qd_gate *gates, int32_t ngates, int32_t plan_kind);
+
+/* ---- readout (Sec. 3.8), FP64 on the device ---------------------------- */
+
+/* sum_i |psi_i|^2 (FP64) into *out (host).  Synchronises. */
+int qd_norm(qd_reg *reg, double *out);
+/* p_i = |psi_i|^2 (FP64) for all N entries into out (QD_HOST or QD_DEVICE
+ * buffer of N doubles). */
+int qd_probabilities(qd_reg *reg, double *out, int32_t where);
+/* P(x_q = v), v < d_q, into the host array out[d_q].  Synchronises. */
+int qd_marginal(qd_reg *reg, int32_t q, double *out);
+/* Inclusive prefix sum of p_i (FP64, left to right) into N doubles. */
+int qd_cdf(qd_reg *reg, double *out, int32_t where);
+/* Measurement sampling: shot s returns the smallest i with
+ * CDF_i > u_s * CDF_{N-1}, u_s = 2^-53 * (word 0 of Philox4x64-10 at
+ * counter (s,0,0,0), key (seed,0)) >> 11).  out: host array of shots int64. */
+int qd_sample(qd_reg *reg, uint64_t seed, int64_t shots, int64_t *out);
+/* The same with caller-supplied uniforms u[0..shots) in [0,1) (host). */
+int qd_sample_u(qd_reg *reg, const double *u, int64_t shots, int64_t *out);
+
+/* Copy the N amplitudes out of / into the register (register precision). */
+int qd_get_amplitudes(qd_reg *reg, void *out, int32_t where);
+int qd_set_amplitudes(qd_reg *reg, const void *in, int32_t where);
+
+/* Wait for the register's stream; report a device-side error word (0 if
+ * none) in *device_error (may be NULL).  Returns QD_ERR_DEVICE if it is set. */
+int qd_sync(qd_reg *reg, int32_t *device_error);
+
+/* Static message for an error code; thread-local message of the last failure. */
+const char *qd_strerror(int code);
+const char *qd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QUDIT_H */

@@ -1,0 +1,1032 @@
+// libqudit C ABI: registers, gate planning and launch, circuits, readout.
+//
+// Gate definitions follow QuDiet (arXiv 2211.07918) Sec. 2.1.2: generalized
+// NOT X^d_{+a}, phase shift Z_d with w = exp(2 pi i/d), generalized Hadamard
+// F_d[j][k] = w^{jk}/sqrt(d), and controlled versions that fire on a control
+// level (d_c - 1 for C_{X,d}, C^n_{X,d}; any chosen level after Fig. 1).
+// Registers follow Sec. 2.2 / Sec. 3.2: N = prod d_q, qudit 0 least
+// significant, initial basis levels.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/qudit.h"
+#include "../../include/qudit_debug.h"
+#include "qd_plan.h"
+#include "qd_reduce.h"
+
+using namespace qd;
+
+// ------------------------------------------------------------------ errors
+
+namespace {
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string &msg) {
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *where) {
+    return fail(QD_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+}  // namespace
+
+#define QD_CUDA(call)                                        \
+    do {                                                     \
+        cudaError_t _e = (call);                             \
+        if (_e != cudaSuccess) return cuda_fail(_e, #call);  \
+    } while (0)
+
+// ---------------------------------------------------------------- register
+
+struct qd_reg {
+    int32_t n = 0;
+    int32_t dims[QD_MAX_QUDITS] = {};
+    int64_t s[QD_MAX_QUDITS + 1] = {};  // s[q] = prod_{p<q} d_p, s[n] = N
+    int64_t N = 0;
+    int32_t prec = QD_C64;
+    size_t esize = 8;
+    void *psi = nullptr;
+    bool owns = false;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int sm_count = 0;
+    double *red = nullptr;  // reduction partials + results
+    size_t red_cap = 0;     // doubles
+    double *cdf = nullptr;  // lazily allocated N doubles
+    double *cdf_chunks = nullptr;
+    int32_t *dev_err = nullptr;
+};
+
+struct qd_plan {
+    qd_reg *reg = nullptr;
+    std::vector<GatePlan> gates;
+    int32_t blocks = 0;
+    bool profile = false;
+    std::vector<cudaEvent_t> events;  // launches + 1 when profiling
+    bool use_graph = true;            // capture on first run, replay afterwards
+    cudaGraphExec_t exec = nullptr;   // captured launches (non-default streams)
+    bool exec_profiled = false;
+    void drop_graph() {
+        if (exec) cudaGraphExecDestroy(exec);
+        exec = nullptr;
+    }
+    ~qd_plan() {
+        drop_graph();
+        for (cudaEvent_t e : events) cudaEventDestroy(e);
+    }
+};
+
+namespace qd {
+int occupancy_blocks(const void *fn, int block, size_t smem) {
+    static std::mutex mu;
+    static std::map<std::pair<const void *, size_t>, int> cache;
+    std::lock_guard<std::mutex> lk(mu);
+    auto key = std::make_pair(fn, smem);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, block, smem) != cudaSuccess || nb < 1) nb = 1;
+    cache[key] = nb;
+    return nb;
+}
+}  // namespace qd
+
+namespace {
+
+int reg_ok(const qd_reg *r) {
+    if (!r) return fail(QD_ERR_ARG, "null register");
+    return QD_OK;
+}
+
+cudaError_t launch_plan(const qd_reg *r, const GatePlan &g) {
+    if (r->prec == QD_C64) return launch_gate_f32(g, r->psi, r->sm_count, r->stream);
+    return launch_gate_f64(g, r->psi, r->sm_count, r->stream);
+}
+
+// ---- gate matrices (Sec. 2.1.2), FP64 -----------------------------------
+
+// w^m for w = exp(2 pi i / d); exponent reduced mod d first, quarter turns exact.
+void omega(int d, long long m, double *re, double *im) {
+    m %= d;
+    if (m < 0) m += d;
+    if ((4 * m) % d == 0) {
+        static const double tr[4] = {1, 0, -1, 0}, ti[4] = {0, 1, 0, -1};
+        const int q = (int)((4 * m) / d);
+        *re = tr[q];
+        *im = ti[q];
+        return;
+    }
+    const double t = 2.0 * M_PI * (double)m / (double)d;
+    *re = std::cos(t);
+    *im = std::sin(t);
+}
+
+std::vector<double> mat_x(int d, int a) {  // column x -> row (x+a) mod d
+    std::vector<double> m(2 * d * d, 0.0);
+    for (int x = 0; x < d; ++x) m[2 * (((x + a) % d) * d + x)] = 1.0;
+    return m;
+}
+
+std::vector<double> mat_z(int d, int p) {
+    std::vector<double> m(2 * d * d, 0.0);
+    for (int j = 0; j < d; ++j) omega(d, (long long)p * j, &m[2 * (j * d + j)], &m[2 * (j * d + j) + 1]);
+    return m;
+}
+
+std::vector<double> mat_f(int d) {
+    std::vector<double> m(2 * d * d, 0.0);
+    const double sc = 1.0 / std::sqrt((double)d);
+    for (int j = 0; j < d; ++j)
+        for (int k = 0; k < d; ++k) {
+            double re, im;
+            omega(d, (long long)j * k, &re, &im);
+            m[2 * (j * d + k)] = re * sc;
+            m[2 * (j * d + k) + 1] = im * sc;
+        }
+    return m;
+}
+
+// ---- validation -----------------------------------------------------------
+
+struct Acting {
+    int k = 0, nc = 0;
+    int t[QD_MAX_TARGETS];
+    int c[QD_MAX_CONTROLS];
+    int lv[QD_MAX_CONTROLS];
+    int D = 1;
+};
+
+int validate(const qd_reg *r, const int32_t *targets, int32_t k, const int32_t *controls, const int32_t *levels,
+             int32_t nc, Acting &a) {
+    if (!targets || k < 1 || k > QD_MAX_TARGETS) return fail(QD_ERR_ARG, "need 1..QD_MAX_TARGETS targets");
+    if (nc < 0 || nc > QD_MAX_CONTROLS || (nc > 0 && !controls)) return fail(QD_ERR_ARG, "bad control list");
+    bool used[QD_MAX_QUDITS] = {};
+    a.k = k;
+    a.nc = nc;
+    a.D = 1;
+    for (int m = 0; m < k; ++m) {
+        const int q = targets[m];
+        if (q < 0 || q >= r->n) return fail(QD_ERR_ARG, "target out of range");
+        if (used[q]) return fail(QD_ERR_OVERLAP, "repeated target");
+        used[q] = true;
+        a.t[m] = q;
+        a.D *= r->dims[q];
+        if (a.D > QD_MAX_D) return fail(QD_ERR_DIM, "target space larger than QD_MAX_D");
+    }
+    for (int m = 0; m < nc; ++m) {
+        const int q = controls[m];
+        if (q < 0 || q >= r->n) return fail(QD_ERR_ARG, "control out of range");
+        if (used[q]) return fail(QD_ERR_OVERLAP, "control repeats a target or control");
+        used[q] = true;
+        int l = levels ? levels[m] : -1;
+        if (l < 0) l = r->dims[q] - 1;
+        if (l >= r->dims[q]) return fail(QD_ERR_ARG, "control level out of range");
+        a.c[m] = q;
+        a.lv[m] = l;
+    }
+    return QD_OK;
+}
+
+// ---- planning of one gate ---------------------------------------------------
+
+void set_expand64(Expand64 &e, const std::vector<std::pair<int64_t, int64_t>> &stride_dim) {
+    e = Expand64{};
+    e.n = (int32_t)stride_dim.size();
+    for (size_t i = 0; i < stride_dim.size(); ++i) {
+        e.div[i] = make_fastdiv64((uint64_t)stride_dim[i].first);
+        e.span[i] = (uint64_t)(stride_dim[i].first * stride_dim[i].second);
+    }
+}
+
+void set_expand32(Expand32 &e, const std::vector<std::pair<int64_t, int64_t>> &stride_dim) {
+    e = Expand32{};
+    e.n = (int32_t)stride_dim.size();
+    for (size_t i = 0; i < stride_dim.size(); ++i) {
+        e.div[i] = make_fastdiv32((uint32_t)stride_dim[i].first);
+        e.span[i] = (uint32_t)(stride_dim[i].first * stride_dim[i].second);
+    }
+}
+
+// Classify M (D x D, interleaved complex): returns true and fills src/lam if
+// every row and every column has exactly one nonzero entry.
+bool classify_mono(const double *M, int D, GatePlan &g) {
+    std::vector<int> colcount(D, 0);
+    for (int i = 0; i < D; ++i) {
+        int nz = -1, cnt = 0;
+        for (int j = 0; j < D; ++j) {
+            const double re = M[2 * (i * D + j)], im = M[2 * (i * D + j) + 1];
+            if (re != 0.0 || im != 0.0) {
+                ++cnt;
+                nz = j;
+            }
+        }
+        if (cnt != 1) return false;
+        if (++colcount[nz] > 1) return false;
+        g.src[i] = nz;
+        g.lam[2 * i] = M[2 * (i * D + nz)];
+        g.lam[2 * i + 1] = M[2 * (i * D + nz) + 1];
+    }
+    g.active = 0;
+    g.unit = 0;
+    for (int i = 0; i < D; ++i) {
+        const bool one = g.lam[2 * i] == 1.0 && g.lam[2 * i + 1] == 0.0;
+        if (one) g.unit |= 1u << i;
+        if (g.src[i] != i || !one) g.active |= 1u << i;
+    }
+    return true;
+}
+
+// Build the launch plan of one gate: matrix M over the targets (first listed
+// most significant), controls at levels.  Returns QD_OK; sets *noop when the
+// gate is the identity.
+int plan_gate(const qd_reg *r, const double *M, const Acting &a, bool diag_only, GatePlan &g, bool *noop) {
+    *noop = false;
+    g = GatePlan{};
+    const int D = a.D;
+    g.D = D;
+    // matrix / classification
+    if (diag_only) {
+        for (int i = 0; i < D; ++i) {
+            g.src[i] = i;
+            g.lam[2 * i] = M[2 * i];
+            g.lam[2 * i + 1] = M[2 * i + 1];
+        }
+        g.active = g.unit = 0;
+        for (int i = 0; i < D; ++i) {
+            const bool one = g.lam[2 * i] == 1.0 && g.lam[2 * i + 1] == 0.0;
+            if (one) g.unit |= 1u << i;
+            else g.active |= 1u << i;
+        }
+        g.kind = Kind::Mono;
+    } else if (classify_mono(M, D, g)) {
+        g.kind = Kind::Mono;
+    } else {
+        g.kind = Kind::Dense;
+        std::memcpy(g.U, M, sizeof(double) * 2 * D * D);
+    }
+    if (g.kind == Kind::Mono && g.active == 0) {
+        *noop = true;
+        return QD_OK;
+    }
+
+    const int n = r->n;
+    const int64_t *s = r->s;
+    bool is_t[QD_MAX_QUDITS] = {}, is_c[QD_MAX_QUDITS] = {};
+    int level[QD_MAX_QUDITS] = {};
+    for (int m = 0; m < a.k; ++m) is_t[a.t[m]] = true;
+    for (int m = 0; m < a.nc; ++m) {
+        is_c[a.c[m]] = true;
+        level[a.c[m]] = a.lv[m];
+    }
+    int64_t cprod = 1;
+    for (int m = 0; m < a.nc; ++m) cprod *= r->dims[a.c[m]];
+
+    // flat offset of local index j: digits of j in the target radices, first target most significant
+    for (int j = 0; j < D; ++j) {
+        int rem = j;
+        int64_t o = 0;
+        for (int m = a.k - 1; m >= 0; --m) {
+            const int t = a.t[m];
+            o += (int64_t)(rem % r->dims[t]) * s[t];
+            rem /= r->dims[t];
+        }
+        g.off[j] = o;
+    }
+    int64_t min_stride = r->N;
+    for (int q = 0; q < n; ++q)
+        if (is_t[q] || is_c[q]) min_stride = std::min<int64_t>(min_stride, s[q]);
+
+    const int64_t touched = r->N / cprod;  // amplitudes in the selected control slice
+    if (g.kind == Kind::Dense) g.alg_bytes = 2.0 * (double)touched * (double)r->esize;
+    else g.alg_bytes = 2.0 * (double)(touched / D) * __builtin_popcount(g.active) * (double)r->esize;
+
+    if (min_stride >= kLowStride) {
+        g.mode = Mode::Direct;
+        g.R = (uint64_t)(r->N / (D * cprod));
+        std::vector<std::pair<int64_t, int64_t>> ins;
+        uint64_t base = 0;
+        for (int q = 0; q < n; ++q)
+            if (is_t[q] || is_c[q]) {
+                ins.push_back({s[q], r->dims[q]});
+                if (is_c[q]) base += (uint64_t)level[q] * (uint64_t)s[q];
+            }
+        set_expand64(g.ex, ins);
+        g.base_off = base;
+        return QD_OK;
+    }
+
+    // ---- tile mode ----
+    g.mode = Mode::Tile;
+    int m = 0;
+    for (int q = 0; q < n; ++q)
+        if ((is_t[q] || is_c[q]) && s[q] < kLowStride) m = q + 1;
+    auto DH_of = [&](int mm) {
+        int64_t dh = 1;
+        for (int q = mm; q < n; ++q)
+            if (is_t[q]) dh *= r->dims[q];
+        return dh;
+    };
+    int64_t B = s[m];
+    int64_t DH = DH_of(m);
+    while (m < n) {
+        const int q = m;
+        const int64_t d = r->dims[q];
+        if (is_t[q]) {
+            B *= d;
+            DH /= d;
+            ++m;
+            continue;
+        }
+        if (is_c[q]) break;
+        const int64_t grown = B * d * DH;
+        if (grown <= (int64_t)kTileBudget || (B < kLowStride && grown <= (int64_t)kTileHardMax)) {
+            B *= d;
+            ++m;
+            continue;
+        }
+        break;
+    }
+    if (B * DH > (int64_t)kTileHardMax) return fail(QD_ERR_UNSUPPORTED, "gate geometry exceeds the tile limit");
+    g.B = (uint32_t)B;
+    g.DH = (uint32_t)DH;
+    // high (>= m) removed digits: expansion over block-level strides s_q / B
+    std::vector<std::pair<int64_t, int64_t>> hi, lo;
+    uint64_t base_hi = 0;
+    uint32_t lo_off = 0;
+    int64_t chi = 1, clo = 1, DL = 1;
+    for (int q = 0; q < n; ++q) {
+        if (!(is_t[q] || is_c[q])) continue;
+        if (q >= m) {
+            hi.push_back({s[q] / B, r->dims[q]});
+            if (is_c[q]) {
+                base_hi += (uint64_t)level[q] * (uint64_t)s[q];
+                chi *= r->dims[q];
+            }
+        } else {
+            lo.push_back({s[q], r->dims[q]});
+            if (is_c[q]) {
+                lo_off += (uint32_t)(level[q] * s[q]);
+                clo *= r->dims[q];
+            } else {
+                DL *= r->dims[q];
+            }
+        }
+    }
+    set_expand64(g.ex_hi, hi);
+    set_expand32(g.ex_lo, lo);
+    g.base_off_hi = base_hi;
+    g.lo_off = lo_off;
+    g.R_tiles = (uint64_t)((r->N / B) / (DH * chi));
+    g.G_in = (uint32_t)(B / (DL * clo));
+    g.tpc = (uint32_t)std::max<int64_t>(1, (int64_t)kTileBudget / (DH * B));
+    if ((uint64_t)g.tpc > g.R_tiles) g.tpc = (uint32_t)std::max<uint64_t>(1, g.R_tiles);
+    g.divB = make_fastdiv32(g.B);
+    g.divG = make_fastdiv32(g.G_in);
+    // chunk offsets: high targets in list order, first listed most significant
+    int th[QD_MAX_TARGETS], nth = 0;
+    for (int mm = 0; mm < a.k; ++mm)
+        if (a.t[mm] >= m) th[nth++] = a.t[mm];
+    for (int h = 0; h < (int)DH; ++h) {
+        int rem = h;
+        int64_t o = 0;
+        for (int i = nth - 1; i >= 0; --i) {
+            o += (int64_t)(rem % r->dims[th[i]]) * s[th[i]];
+            rem /= r->dims[th[i]];
+        }
+        g.offH[h] = o;
+    }
+    // shared-memory offsets of local index j: chunk index (high digits) * B + low offset
+    for (int j = 0; j < D; ++j) {
+        int rem = j;
+        int64_t h = 0, hmul = 1, offl = 0;
+        for (int mm = a.k - 1; mm >= 0; --mm) {
+            const int t = a.t[mm];
+            const int x = rem % r->dims[t];
+            rem /= r->dims[t];
+            if (t >= m) {
+                h += x * hmul;
+                hmul *= r->dims[t];
+            } else {
+                offl += (int64_t)x * s[t];
+            }
+        }
+        g.smoff[j] = (int32_t)(h * B + offl);
+    }
+    return QD_OK;
+}
+
+int gate_matrix(const qd_reg *r, const qd_gate *gt, const Acting &a, std::vector<double> &M, bool *diag) {
+    *diag = false;
+    switch (gt->kind) {
+        case QD_GATE_X: {
+            if (a.k != 1) return fail(QD_ERR_ARG, "X acts on one qudit");
+            const int d = r->dims[a.t[0]];
+            if (gt->param < 1 || gt->param > d - 1) return fail(QD_ERR_ARG, "X shift must be in [1, d-1]");
+            M = mat_x(d, gt->param);
+            return QD_OK;
+        }
+        case QD_GATE_Z:
+            if (a.k != 1) return fail(QD_ERR_ARG, "Z acts on one qudit");
+            M = mat_z(r->dims[a.t[0]], gt->param);
+            return QD_OK;
+        case QD_GATE_H:
+            if (a.k != 1) return fail(QD_ERR_ARG, "H acts on one qudit");
+            M = mat_f(r->dims[a.t[0]]);
+            return QD_OK;
+        case QD_GATE_U:
+            if (!gt->matrix) return fail(QD_ERR_ARG, "U gate without matrix");
+            M.assign(gt->matrix, gt->matrix + 2 * a.D * a.D);
+            return QD_OK;
+        case QD_GATE_DIAG:
+            if (!gt->matrix) return fail(QD_ERR_ARG, "DIAG gate without entries");
+            M.assign(gt->matrix, gt->matrix + 2 * a.D);
+            *diag = true;
+            return QD_OK;
+        default:
+            return fail(QD_ERR_ARG, "unknown gate kind");
+    }
+}
+
+int prepare_gate(const qd_reg *r, const qd_gate *gt, GatePlan &g, bool *noop) {
+    if (!gt) return fail(QD_ERR_ARG, "null gate");
+    Acting a;
+    int rc = validate(r, gt->targets, gt->k, gt->controls, gt->ctrl_levels, gt->nc, a);
+    if (rc) return rc;
+    std::vector<double> M;
+    bool diag = false;
+    if ((rc = gate_matrix(r, gt, a, M, &diag))) return rc;
+    return plan_gate(r, M.data(), a, diag, g, noop);
+}
+
+int apply_record(qd_reg *r, const qd_gate *gt) {
+    GatePlan g;
+    bool noop = false;
+    int rc = prepare_gate(r, gt, g, &noop);
+    if (rc) return rc;
+    if (noop) return QD_OK;
+    cudaError_t e = launch_plan(r, g);
+    if (e != cudaSuccess) return cuda_fail(e, "gate launch");
+    return QD_OK;
+}
+
+qd_gate make_record(int kind, const int32_t *targets, int32_t k, const int32_t *controls, const int32_t *levels,
+                    int32_t nc, int32_t param, const double *matrix) {
+    qd_gate g;
+    std::memset(&g, 0, sizeof(g));
+    g.kind = kind;
+    g.k = k;
+    for (int i = 0; i < k && i < QD_MAX_TARGETS; ++i) g.targets[i] = targets[i];
+    g.nc = nc;
+    for (int i = 0; i < nc && i < QD_MAX_CONTROLS; ++i) {
+        g.controls[i] = controls[i];
+        g.ctrl_levels[i] = levels ? levels[i] : -1;
+    }
+    g.param = param;
+    g.matrix = matrix;
+    return g;
+}
+
+int ensure_red(qd_reg *r, size_t doubles) {
+    if (r->red_cap >= doubles) return QD_OK;
+    if (r->red) cudaFree(r->red);
+    r->red = nullptr;
+    r->red_cap = 0;
+    if (cudaMalloc(&r->red, doubles * sizeof(double)) != cudaSuccess)
+        return fail(QD_ERR_OOM, "reduction scratch allocation failed");
+    r->red_cap = doubles;
+    return QD_OK;
+}
+
+int ensure_cdf(qd_reg *r) {
+    if (r->cdf) return QD_OK;
+    const size_t nch = cdf_chunks((uint64_t)r->N) + 1;
+    if (cudaMalloc(&r->cdf, (size_t)r->N * sizeof(double)) != cudaSuccess) {
+        r->cdf = nullptr;
+        return fail(QD_ERR_OOM, "CDF buffer allocation failed");
+    }
+    if (cudaMalloc(&r->cdf_chunks, nch * sizeof(double)) != cudaSuccess) {
+        cudaFree(r->cdf);
+        r->cdf = nullptr;
+        r->cdf_chunks = nullptr;
+        return fail(QD_ERR_OOM, "CDF chunk allocation failed");
+    }
+    return QD_OK;
+}
+
+int compute_cdf(qd_reg *r) {
+    int rc = ensure_cdf(r);
+    if (rc) return rc;
+    QD_CUDA(cdf(r->psi, r->prec, (uint64_t)r->N, r->cdf_chunks, r->cdf, r->stream));
+    return QD_OK;
+}
+
+}  // namespace
+
+// ====================================================================== ABI
+
+extern "C" {
+
+const char *qd_strerror(int code) {
+    switch (code) {
+        case QD_OK: return "ok";
+        case QD_ERR_ARG: return "invalid argument";
+        case QD_ERR_DIM: return "dimension out of range";
+        case QD_ERR_OVERLAP: return "overlapping qudits";
+        case QD_ERR_OOM: return "out of memory";
+        case QD_ERR_CUDA: return "CUDA error";
+        case QD_ERR_TIMEOUT: return "device wait timed out";
+        case QD_ERR_DEVICE: return "device reported an error";
+        case QD_ERR_UNSUPPORTED: return "unsupported";
+        default: return "unknown error";
+    }
+}
+
+const char *qd_last_error(void) { return g_last_error.c_str(); }
+
+int qd_create(const int32_t *dims, int32_t n, const int32_t *init_levels, int32_t precision, void *dev_buf,
+              size_t dev_buf_bytes, void *stream, qd_reg **out) {
+    if (!out) return fail(QD_ERR_ARG, "null output handle");
+    *out = nullptr;
+    if (!dims || n < 1 || n > QD_MAX_QUDITS) return fail(QD_ERR_ARG, "need 1..QD_MAX_QUDITS dims");
+    if (precision != QD_C64 && precision != QD_C128) return fail(QD_ERR_ARG, "precision must be QD_C64 or QD_C128");
+    int64_t N = 1;
+    for (int q = 0; q < n; ++q) {
+        if (dims[q] < 2 || dims[q] > 64) return fail(QD_ERR_DIM, "qudit dimension must be in [2, 64]");
+        if (N > QD_MAX_AMPLITUDES / dims[q]) return fail(QD_ERR_DIM, "register larger than QD_MAX_AMPLITUDES");
+        N *= dims[q];
+    }
+    int64_t idx = 0;
+    {
+        int64_t s = 1;
+        for (int q = 0; q < n; ++q) {
+            const int l = init_levels ? init_levels[q] : 0;
+            if (l < 0 || l >= dims[q]) return fail(QD_ERR_ARG, "init level out of range");
+            idx += (int64_t)l * s;
+            s *= dims[q];
+        }
+    }
+    qd_reg *r = new qd_reg();
+    r->n = n;
+    int64_t s = 1;
+    for (int q = 0; q < n; ++q) {
+        r->dims[q] = dims[q];
+        r->s[q] = s;
+        s *= dims[q];
+    }
+    r->s[n] = s;
+    r->N = N;
+    r->prec = precision;
+    r->esize = precision == QD_C64 ? 8 : 16;
+    r->stream = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaGetDevice(&r->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&r->sm_count, cudaDevAttrMultiProcessorCount, r->device);
+    if (e != cudaSuccess) {
+        delete r;
+        return cuda_fail(e, "device query");
+    }
+    const size_t bytes = (size_t)N * r->esize;
+    if (dev_buf) {
+        if (dev_buf_bytes < bytes) {
+            delete r;
+            return fail(QD_ERR_OOM, "caller buffer smaller than N amplitudes");
+        }
+        if (reinterpret_cast<uintptr_t>(dev_buf) % 16 != 0) {
+            delete r;
+            return fail(QD_ERR_ARG, "caller buffer must be 16-byte aligned");
+        }
+        r->psi = dev_buf;
+        r->owns = false;
+    } else {
+        if (cudaMalloc(&r->psi, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            delete r;
+            return fail(QD_ERR_OOM, "state allocation failed");
+        }
+        r->owns = true;
+    }
+    if (cudaMalloc(&r->dev_err, sizeof(int32_t)) != cudaSuccess ||
+        cudaMemsetAsync(r->dev_err, 0, sizeof(int32_t), r->stream) != cudaSuccess) {
+        cudaGetLastError();
+        qd_destroy(r);
+        return fail(QD_ERR_OOM, "error word allocation failed");
+    }
+    int rc = ensure_red(r, (size_t)reduce_blocks(r->sm_count) * 64 + 64);
+    if (rc) {
+        qd_destroy(r);
+        return rc;
+    }
+    e = init_basis(r->psi, r->prec, (uint64_t)N, (uint64_t)idx, r->sm_count, r->stream);
+    if (e != cudaSuccess) {
+        qd_destroy(r);
+        return cuda_fail(e, "init");
+    }
+    *out = r;
+    return QD_OK;
+}
+
+int qd_destroy(qd_reg *r) {
+    if (!r) return QD_OK;
+    if (r->stream) cudaStreamSynchronize(r->stream);
+    else cudaDeviceSynchronize();
+    if (r->owns && r->psi) cudaFree(r->psi);
+    if (r->red) cudaFree(r->red);
+    if (r->cdf) cudaFree(r->cdf);
+    if (r->cdf_chunks) cudaFree(r->cdf_chunks);
+    if (r->dev_err) cudaFree(r->dev_err);
+    delete r;
+    return QD_OK;
+}
+
+int qd_reset(qd_reg *r, const int32_t *init_levels) {
+    if (int rc = reg_ok(r)) return rc;
+    int64_t idx = 0;
+    for (int q = 0; q < r->n; ++q) {
+        const int l = init_levels ? init_levels[q] : 0;
+        if (l < 0 || l >= r->dims[q]) return fail(QD_ERR_ARG, "init level out of range");
+        idx += (int64_t)l * r->s[q];
+    }
+    QD_CUDA(init_basis(r->psi, r->prec, (uint64_t)r->N, (uint64_t)idx, r->sm_count, r->stream));
+    return QD_OK;
+}
+
+int qd_info(const qd_reg *r, int64_t *N, int32_t *n, void **state, int32_t *precision) {
+    if (int rc = reg_ok(r)) return rc;
+    if (N) *N = r->N;
+    if (n) *n = r->n;
+    if (state) *state = r->psi;
+    if (precision) *precision = r->prec;
+    return QD_OK;
+}
+
+int qd_set_stream(qd_reg *r, void *stream) {
+    if (int rc = reg_ok(r)) return rc;
+    r->stream = static_cast<cudaStream_t>(stream);
+    return QD_OK;
+}
+
+int qd_apply(qd_reg *r, const double *matrix, const int32_t *targets, int32_t k, const int32_t *controls,
+             const int32_t *ctrl_levels, int32_t nc) {
+    if (int rc = reg_ok(r)) return rc;
+    if (!targets || k < 1 || k > QD_MAX_TARGETS) return fail(QD_ERR_ARG, "need 1..QD_MAX_TARGETS targets");
+    qd_gate g = make_record(QD_GATE_U, targets, k, controls, ctrl_levels, nc, 0, matrix);
+    return apply_record(r, &g);
+}
+
+int qd_apply_diag(qd_reg *r, const double *diag, const int32_t *targets, int32_t k, const int32_t *controls,
+                  const int32_t *ctrl_levels, int32_t nc) {
+    if (int rc = reg_ok(r)) return rc;
+    if (!targets || k < 1 || k > QD_MAX_TARGETS) return fail(QD_ERR_ARG, "need 1..QD_MAX_TARGETS targets");
+    qd_gate g = make_record(QD_GATE_DIAG, targets, k, controls, ctrl_levels, nc, 0, diag);
+    return apply_record(r, &g);
+}
+
+int qd_apply_x(qd_reg *r, int32_t t, int32_t shift) {
+    if (int rc = reg_ok(r)) return rc;
+    qd_gate g = make_record(QD_GATE_X, &t, 1, nullptr, nullptr, 0, shift, nullptr);
+    return apply_record(r, &g);
+}
+
+int qd_apply_z(qd_reg *r, int32_t t, int32_t power) {
+    if (int rc = reg_ok(r)) return rc;
+    qd_gate g = make_record(QD_GATE_Z, &t, 1, nullptr, nullptr, 0, power, nullptr);
+    return apply_record(r, &g);
+}
+
+int qd_apply_h(qd_reg *r, int32_t t) {
+    if (int rc = reg_ok(r)) return rc;
+    qd_gate g = make_record(QD_GATE_H, &t, 1, nullptr, nullptr, 0, 0, nullptr);
+    return apply_record(r, &g);
+}
+
+int qd_apply_cx(qd_reg *r, int32_t c, int32_t t, int32_t shift, int32_t ctrl_level) {
+    if (int rc = reg_ok(r)) return rc;
+    qd_gate g = make_record(QD_GATE_X, &t, 1, &c, &ctrl_level, 1, shift, nullptr);
+    return apply_record(r, &g);
+}
+
+int qd_apply_mct(qd_reg *r, const int32_t *controls, const int32_t *ctrl_levels, int32_t nc, int32_t t,
+                 int32_t shift) {
+    if (int rc = reg_ok(r)) return rc;
+    if (nc < 0 || nc > QD_MAX_CONTROLS || (nc > 0 && !controls)) return fail(QD_ERR_ARG, "bad control list");
+    qd_gate g = make_record(QD_GATE_X, &t, 1, controls, ctrl_levels, nc, shift, nullptr);
+    return apply_record(r, &g);
+}
+
+int qd_apply_gate(qd_reg *r, const qd_gate *gate) {
+    if (int rc = reg_ok(r)) return rc;
+    return apply_record(r, gate);
+}
+
+int qd_plan_create(qd_reg *r, const qd_gate *gates, int32_t ngates, int32_t plan_kind, qd_plan **out) {
+    if (!out) return fail(QD_ERR_ARG, "null output handle");
+    *out = nullptr;
+    if (int rc = reg_ok(r)) return rc;
+    if (ngates < 0 || (ngates > 0 && !gates)) return fail(QD_ERR_ARG, "bad gate list");
+    if (plan_kind != QD_PLAN_NONE) return fail(QD_ERR_UNSUPPORTED, "fusion plans are not built in this library yet");
+    qd_plan *p = new qd_plan();
+    p->reg = r;
+    p->gates.reserve(ngates);
+    for (int i = 0; i < ngates; ++i) {
+        GatePlan g;
+        bool noop = false;
+        int rc = prepare_gate(r, &gates[i], g, &noop);
+        if (rc) {
+            delete p;
+            g_last_error = "gate " + std::to_string(i) + ": " + g_last_error;
+            return rc;
+        }
+        if (!noop) p->gates.push_back(g);
+    }
+    *out = p;
+    return QD_OK;
+}
+
+namespace {
+// Enqueue every launch of the plan (and, when profiling, an event before each
+// launch and after the last) on stream s.
+cudaError_t enqueue_plan(qd_plan *p, cudaStream_t s) {
+    const bool prof = p->profile && p->events.size() == p->gates.size() + 1;
+    qd_reg tmp = *p->reg;
+    tmp.stream = s;
+    for (size_t i = 0; i < p->gates.size(); ++i) {
+        if (prof) {
+            cudaError_t e = cudaEventRecord(p->events[i], s);
+            if (e != cudaSuccess) return e;
+        }
+        cudaError_t e = launch_plan(&tmp, p->gates[i]);
+        if (e != cudaSuccess) return e;
+    }
+    if (prof) return cudaEventRecord(p->events[p->gates.size()], s);
+    return cudaSuccess;
+}
+}  // namespace
+
+int qd_plan_run(qd_plan *p) {
+    if (!p) return fail(QD_ERR_ARG, "null plan");
+    cudaStream_t s = p->reg->stream;
+    if (!s || !p->use_graph) {  // the legacy default stream cannot be captured: launch directly
+        cudaError_t e = enqueue_plan(p, s);
+        if (e != cudaSuccess) return cuda_fail(e, "gate launch");
+        return QD_OK;
+    }
+    if (!p->exec || p->exec_profiled != p->profile) {
+        p->drop_graph();
+        QD_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = enqueue_plan(p, s);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(s, &graph);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            return cuda_fail(e != cudaSuccess ? e : e2, "plan capture");
+        }
+        e = cudaGraphInstantiate(&p->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            p->exec = nullptr;
+            return cuda_fail(e, "graph instantiate");
+        }
+        p->exec_profiled = p->profile;
+    }
+    QD_CUDA(cudaGraphLaunch(p->exec, s));
+    return QD_OK;
+}
+
+int qd_plan_profile(qd_plan *p, int32_t enable) {
+    if (!p) return fail(QD_ERR_ARG, "null plan");
+    p->profile = enable != 0;
+    if (p->profile && p->events.size() != p->gates.size() + 1) {
+        for (cudaEvent_t e : p->events) cudaEventDestroy(e);
+        p->events.clear();
+        for (size_t i = 0; i <= p->gates.size(); ++i) {
+            cudaEvent_t e;
+            QD_CUDA(cudaEventCreate(&e));
+            p->events.push_back(e);
+        }
+    }
+    return QD_OK;
+}
+
+int qd_plan_timings(qd_plan *p, float *ms, double *alg_bytes, int32_t *kclass) {
+    if (!p) return fail(QD_ERR_ARG, "null plan");
+    const size_t n = p->gates.size();
+    if (ms) {
+        if (!p->profile || p->events.size() != n + 1) return fail(QD_ERR_ARG, "profiling is not enabled");
+        QD_CUDA(cudaStreamSynchronize(p->reg->stream));
+        for (size_t i = 0; i < n; ++i) QD_CUDA(cudaEventElapsedTime(&ms[i], p->events[i], p->events[i + 1]));
+    }
+    for (size_t i = 0; i < n; ++i) {
+        const GatePlan &g = p->gates[i];
+        if (alg_bytes) alg_bytes[i] = g.alg_bytes;
+        if (kclass) {
+            int c = g.kind == Kind::Dense ? (g.mode == Mode::Direct ? QD_KCLASS_DENSE_DIRECT : QD_KCLASS_DENSE_TILE)
+                                          : (g.mode == Mode::Direct ? QD_KCLASS_MONO_DIRECT : QD_KCLASS_MONO_TILE);
+            kclass[i] = c | (g.D << 8);
+        }
+    }
+    return QD_OK;
+}
+
+int qd_plan_info(const qd_plan *p, int32_t *launches, int32_t *blocks) {
+    if (!p) return fail(QD_ERR_ARG, "null plan");
+    if (launches) *launches = (int32_t)p->gates.size();
+    if (blocks) *blocks = p->blocks;
+    return QD_OK;
+}
+
+int qd_plan_destroy(qd_plan *p) {
+    delete p;
+    return QD_OK;
+}
+
+int qd_run_circuit(qd_reg *r, const qd_gate *gates, int32_t ngates, int32_t plan_kind) {
+    qd_plan *p = nullptr;
+    int rc = qd_plan_create(r, gates, ngates, plan_kind, &p);
+    if (rc) return rc;
+    p->use_graph = false;  // one run: direct launches, no capture cost
+    rc = qd_plan_run(p);
+    qd_plan_destroy(p);
+    return rc;
+}
+
+int qd_norm(qd_reg *r, double *out) {
+    if (int rc = reg_ok(r)) return rc;
+    if (!out) return fail(QD_ERR_ARG, "null output");
+    const int nb = reduce_blocks(r->sm_count);
+    Expand64 ex{};
+    double *res = r->red + nb * 64;
+    QD_CUDA(slice_norms(r->psi, r->prec, (uint64_t)r->N, ex, 0, 1, r->red, nb, res, r->stream));
+    QD_CUDA(cudaMemcpyAsync(out, res, sizeof(double), cudaMemcpyDeviceToHost, r->stream));
+    QD_CUDA(cudaStreamSynchronize(r->stream));
+    return QD_OK;
+}
+
+int qd_marginal(qd_reg *r, int32_t q, double *out) {
+    if (int rc = reg_ok(r)) return rc;
+    if (!out) return fail(QD_ERR_ARG, "null output");
+    if (q < 0 || q >= r->n) return fail(QD_ERR_ARG, "qudit out of range");
+    const int nb = reduce_blocks(r->sm_count);
+    const int d = r->dims[q];
+    Expand64 ex{};
+    set_expand64(ex, {{r->s[q], d}});
+    double *res = r->red + (size_t)nb * 64;
+    QD_CUDA(slice_norms(r->psi, r->prec, (uint64_t)(r->N / d), ex, (uint64_t)r->s[q], d, r->red, nb, res, r->stream));
+    QD_CUDA(cudaMemcpyAsync(out, res, sizeof(double) * d, cudaMemcpyDeviceToHost, r->stream));
+    QD_CUDA(cudaStreamSynchronize(r->stream));
+    return QD_OK;
+}
+
+int qd_probabilities(qd_reg *r, double *out, int32_t where) {
+    if (int rc = reg_ok(r)) return rc;
+    if (!out) return fail(QD_ERR_ARG, "null output");
+    if (where == QD_DEVICE) {
+        QD_CUDA(probabilities(r->psi, r->prec, (uint64_t)r->N, out, r->sm_count, r->stream));
+        return QD_OK;
+    }
+    if (where != QD_HOST) return fail(QD_ERR_ARG, "where must be QD_HOST or QD_DEVICE");
+    int rc = ensure_cdf(r);  // reuse the CDF buffer as staging
+    if (rc) return rc;
+    QD_CUDA(probabilities(r->psi, r->prec, (uint64_t)r->N, r->cdf, r->sm_count, r->stream));
+    QD_CUDA(cudaMemcpyAsync(out, r->cdf, sizeof(double) * r->N, cudaMemcpyDeviceToHost, r->stream));
+    QD_CUDA(cudaStreamSynchronize(r->stream));
+    return QD_OK;
+}
+
+int qd_cdf(qd_reg *r, double *out, int32_t where) {
+    if (int rc = reg_ok(r)) return rc;
+    if (!out) return fail(QD_ERR_ARG, "null output");
+    if (where != QD_HOST && where != QD_DEVICE) return fail(QD_ERR_ARG, "where must be QD_HOST or QD_DEVICE");
+    int rc = compute_cdf(r);
+    if (rc) return rc;
+    QD_CUDA(cudaMemcpyAsync(out, r->cdf, sizeof(double) * r->N,
+                            where == QD_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, r->stream));
+    if (where == QD_HOST) QD_CUDA(cudaStreamSynchronize(r->stream));
+    return QD_OK;
+}
+
+static int sample_impl(qd_reg *r, const double *u_host, uint64_t seed, int64_t shots, int64_t *out) {
+    if (int rc = reg_ok(r)) return rc;
+    if (!out || shots < 0) return fail(QD_ERR_ARG, "bad sample arguments");
+    if (shots == 0) return QD_OK;
+    int rc = compute_cdf(r);
+    if (rc) return rc;
+    double *u_dev = nullptr;
+    int64_t *o_dev = nullptr;
+    if (u_host && cudaMalloc(&u_dev, sizeof(double) * shots) != cudaSuccess) return fail(QD_ERR_OOM, "sample buffer");
+    if (cudaMalloc(&o_dev, sizeof(int64_t) * shots) != cudaSuccess) {
+        if (u_dev) cudaFree(u_dev);
+        return fail(QD_ERR_OOM, "sample buffer");
+    }
+    cudaError_t e = cudaSuccess;
+    if (u_host) e = cudaMemcpyAsync(u_dev, u_host, sizeof(double) * shots, cudaMemcpyHostToDevice, r->stream);
+    if (e == cudaSuccess) e = sample(r->cdf, (uint64_t)r->N, u_dev, seed, shots, o_dev, r->sm_count, r->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, o_dev, sizeof(int64_t) * shots, cudaMemcpyDeviceToHost, r->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
+    if (u_dev) cudaFree(u_dev);
+    cudaFree(o_dev);
+    if (e != cudaSuccess) return cuda_fail(e, "sample");
+    return QD_OK;
+}
+
+int qd_sample(qd_reg *r, uint64_t seed, int64_t shots, int64_t *out) { return sample_impl(r, nullptr, seed, shots, out); }
+
+int qd_sample_u(qd_reg *r, const double *u, int64_t shots, int64_t *out) {
+    if (!u) return fail(QD_ERR_ARG, "null uniforms");
+    return sample_impl(r, u, 0, shots, out);
+}
+
+int qd_get_amplitudes(qd_reg *r, void *out, int32_t where) {
+    if (int rc = reg_ok(r)) return rc;
+    if (!out) return fail(QD_ERR_ARG, "null output");
+    if (where != QD_HOST && where != QD_DEVICE) return fail(QD_ERR_ARG, "where must be QD_HOST or QD_DEVICE");
+    QD_CUDA(cudaMemcpyAsync(out, r->psi, r->esize * r->N,
+                            where == QD_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, r->stream));
+    if (where == QD_HOST) QD_CUDA(cudaStreamSynchronize(r->stream));
+    return QD_OK;
+}
+
+int qd_set_amplitudes(qd_reg *r, const void *in, int32_t where) {
+    if (int rc = reg_ok(r)) return rc;
+    if (!in) return fail(QD_ERR_ARG, "null input");
+    if (where != QD_HOST && where != QD_DEVICE) return fail(QD_ERR_ARG, "where must be QD_HOST or QD_DEVICE");
+    QD_CUDA(cudaMemcpyAsync(r->psi, in, r->esize * r->N,
+                            where == QD_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, r->stream));
+    return QD_OK;
+}
+
+int qd_sync(qd_reg *r, int32_t *device_error) {
+    if (int rc = reg_ok(r)) return rc;
+    int32_t err = 0;
+    QD_CUDA(cudaMemcpyAsync(&err, r->dev_err, sizeof(int32_t), cudaMemcpyDeviceToHost, r->stream));
+    QD_CUDA(cudaStreamSynchronize(r->stream));
+    if (device_error) *device_error = err;
+    if (err) return fail(QD_ERR_DEVICE, "device error word set: " + std::to_string(err));
+    return QD_OK;
+}
+
+int qd_debug_gate_members(const int32_t *dims, int32_t n, const qd_gate *gate, int64_t *out, int64_t cap,
+                          int64_t *info) {
+    if (!dims || n < 1 || n > QD_MAX_QUDITS || !info) return fail(QD_ERR_ARG, "bad arguments");
+    qd_reg r;
+    r.n = n;
+    int64_t s = 1;
+    for (int q = 0; q < n; ++q) {
+        if (dims[q] < 2 || dims[q] > 64) return fail(QD_ERR_DIM, "qudit dimension must be in [2, 64]");
+        r.dims[q] = dims[q];
+        r.s[q] = s;
+        s *= dims[q];
+    }
+    r.s[n] = s;
+    r.N = s;
+    r.esize = 8;
+    GatePlan g;
+    bool noop = false;
+    int rc = prepare_gate(&r, gate, g, &noop);
+    if (rc) return rc;
+    for (int i = 0; i < 7; ++i) info[i] = 0;
+    info[6] = noop ? 1 : 0;
+    if (noop) return QD_OK;
+    const int D = g.D;
+    info[0] = g.mode == Mode::Tile ? 1 : 0;
+    info[1] = D;
+    info[3] = g.kind == Kind::Mono ? 1 : 0;
+    info[4] = g.active;
+    info[5] = g.B;
+    int64_t w = 0;
+    auto put = [&](int64_t v) {
+        if (out && w < cap) out[w] = v;
+        ++w;
+    };
+    if (g.mode == Mode::Direct) {
+        info[2] = (int64_t)g.R;
+        for (uint64_t gi = 0; gi < g.R; ++gi) {
+            const uint64_t base = expand(gi, g.ex) + g.base_off;
+            for (int j = 0; j < D; ++j) put((int64_t)(base + g.off[j]));
+        }
+        return QD_OK;
+    }
+    info[2] = (int64_t)(g.R_tiles * g.G_in);
+    std::vector<uint64_t> cb(g.DH);
+    for (uint64_t t = 0; t < g.R_tiles; ++t) {
+        for (uint32_t h = 0; h < g.DH; ++h) cb[h] = expand(t, g.ex_hi) * g.B + g.base_off_hi + g.offH[h];
+        for (uint32_t gl = 0; gl < g.G_in; ++gl) {
+            const uint32_t eb = expand(gl, g.ex_lo) + g.lo_off;
+            for (int j = 0; j < D; ++j) {
+                const uint32_t p = eb + (uint32_t)g.smoff[j];
+                const uint32_t c = fdiv(p, g.divB);
+                put((int64_t)(cb[c] + (p - c * g.B)));
+            }
+        }
+    }
+    return QD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,64 @@
+// Host-side description of one prepared gate launch (precision independent).
+// Built by the planner in qd_api.cu, consumed by the per-precision launchers.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "qd_common.cuh"
+
+namespace qd {
+
+enum class Mode : int32_t { Direct = 0, Tile = 1 };
+enum class Kind : int32_t { Dense = 0, Mono = 1 };
+
+// Largest number of amplitudes a tile-mode CTA stages in shared memory per
+// iteration, and the hard cap when the block length must be raised to reach
+// a coalescing width.
+constexpr uint32_t kTileBudget = 2048;
+constexpr uint32_t kTileHardMax = 8192;
+// A target or control qudit with flat stride below this many amplitudes makes
+// the direct kernel's warps read short strided runs; such gates use tile mode.
+constexpr int64_t kLowStride = 32;
+
+struct GatePlan {
+    Mode mode = Mode::Direct;
+    Kind kind = Kind::Dense;
+    int32_t D = 0;
+
+    // --- direct mode: one thread per group --------------------------------
+    uint64_t R = 0;          // number of groups
+    uint64_t base_off = 0;   // sum over controls of level * stride
+    Expand64 ex{};           // group index -> flat base
+    int64_t off[kMaxD] = {}; // flat offset of local index j
+
+    // --- tile mode: a CTA stages DH chunks of B contiguous amplitudes -------
+    uint64_t R_tiles = 0;      // number of tiles
+    uint64_t base_off_hi = 0;  // controls at or above the block, level * stride
+    Expand64 ex_hi{};          // tile index -> flat tile base (already scaled by B)
+    uint32_t B = 0;            // block length (amplitudes), = s_m
+    uint32_t DH = 0;           // combinations of the targets at or above the block
+    uint32_t tpc = 0;          // tiles per CTA iteration
+    uint32_t G_in = 0;         // groups per tile
+    FastDiv32 divB{};          // element index -> chunk
+    FastDiv32 divG{};          // group index -> tile
+    Expand32 ex_lo{};          // in-tile group index -> position inside the block
+    uint32_t lo_off = 0;       // controls below the block, level * stride
+    int64_t offH[kMaxD] = {};  // flat offset of chunk h
+    int32_t smoff[kMaxD] = {}; // shared-memory offset of local index j in a tile
+
+    // --- numerics (FP64, rounded to the state precision at launch) ---------
+    double U[2 * kMaxD * kMaxD] = {};  // dense: row-major D x D (re, im)
+    int32_t src[kMaxD] = {};           // mono: out[i] = lam[i] * in[src[i]]
+    double lam[2 * kMaxD] = {};
+    uint32_t active = 0;               // mono: bit i set if out[i] != in[i]
+    uint32_t unit = 0;                 // mono: bit i set if lam[i] == 1 exactly
+
+    // --- accounting --------------------------------------------------------
+    double alg_bytes = 0;  // algorithmic HBM bytes of one launch
+};
+
+// Per-precision launchers (qd_apply_f32.cu / qd_apply_f64.cu).
+cudaError_t launch_gate_f32(const GatePlan &g, void *psi, int sm_count, cudaStream_t s);
+cudaError_t launch_gate_f64(const GatePlan &g, void *psi, int sm_count, cudaStream_t s);
+
+}  // namespace qd

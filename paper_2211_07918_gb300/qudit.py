@@ -1,0 +1,422 @@
+"""ctypes binding of libqudit (include/qudit.h).
+
+Argument marshalling only: every call goes straight to the C ABI of the CUDA
+library, under the same name; failures raise :class:`QuditError` with the
+library's message.  There is no other implementation behind these names: if
+libqudit.so is missing or cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from .build import LIB_PATH
+
+# ---- constants mirrored from include/qudit.h ----------------------------
+QD_OK = 0
+QD_C64, QD_C128 = 1, 2
+QD_HOST, QD_DEVICE = 0, 1
+QD_GATE_X, QD_GATE_Z, QD_GATE_H, QD_GATE_U, QD_GATE_DIAG = 1, 2, 3, 4, 5
+QD_PLAN_NONE, QD_PLAN_GREEDY, QD_PLAN_LEARNED, QD_PLAN_EXHAUSTIVE = 0, 1, 2, 3
+QD_MAX_TARGETS, QD_MAX_CONTROLS = 6, 8
+ERRORS = {-1: "QD_ERR_ARG", -2: "QD_ERR_DIM", -3: "QD_ERR_OVERLAP", -4: "QD_ERR_OOM", -5: "QD_ERR_CUDA",
+          -6: "QD_ERR_TIMEOUT", -7: "QD_ERR_DEVICE", -8: "QD_ERR_UNSUPPORTED"}
+
+_i32 = ctypes.c_int32
+_i64 = ctypes.c_int64
+_dp = ctypes.POINTER(ctypes.c_double)
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_vp = ctypes.c_void_p
+
+
+class QdGate(ctypes.Structure):
+    _fields_ = [("kind", _i32), ("k", _i32), ("targets", _i32 * QD_MAX_TARGETS), ("nc", _i32),
+                ("controls", _i32 * QD_MAX_CONTROLS), ("ctrl_levels", _i32 * QD_MAX_CONTROLS),
+                ("param", _i32), ("reserved", _i32), ("matrix", _dp)]
+
+
+class QuditError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+# (name, argtypes) for every exported call; restype is int unless noted
+_SIGS = {
+    "qd_create": [_i32p, _i32, _i32p, _i32, _vp, ctypes.c_size_t, _vp, ctypes.POINTER(_vp)],
+    "qd_destroy": [_vp],
+    "qd_reset": [_vp, _i32p],
+    "qd_info": [_vp, _i64p, _i32p, ctypes.POINTER(_vp), _i32p],
+    "qd_set_stream": [_vp, _vp],
+    "qd_apply": [_vp, _dp, _i32p, _i32, _i32p, _i32p, _i32],
+    "qd_apply_diag": [_vp, _dp, _i32p, _i32, _i32p, _i32p, _i32],
+    "qd_apply_x": [_vp, _i32, _i32],
+    "qd_apply_z": [_vp, _i32, _i32],
+    "qd_apply_h": [_vp, _i32],
+    "qd_apply_cx": [_vp, _i32, _i32, _i32, _i32],
+    "qd_apply_mct": [_vp, _i32p, _i32p, _i32, _i32, _i32],
+    "qd_apply_gate": [_vp, ctypes.POINTER(QdGate)],
+    "qd_plan_create": [_vp, ctypes.POINTER(QdGate), _i32, _i32, ctypes.POINTER(_vp)],
+    "qd_plan_run": [_vp],
+    "qd_plan_info": [_vp, _i32p, _i32p],
+    "qd_plan_destroy": [_vp],
+    "qd_plan_profile": [_vp, _i32],
+    "qd_plan_timings": [_vp, ctypes.POINTER(ctypes.c_float), _dp, _i32p],
+    "qd_run_circuit": [_vp, ctypes.POINTER(QdGate), _i32, _i32],
+    "qd_norm": [_vp, _dp],
+    "qd_probabilities": [_vp, _dp, _i32],
+    "qd_marginal": [_vp, _i32, _dp],
+    "qd_cdf": [_vp, _dp, _i32],
+    "qd_sample": [_vp, ctypes.c_uint64, _i64, _i64p],
+    "qd_sample_u": [_vp, _dp, _i64, _i64p],
+    "qd_get_amplitudes": [_vp, _vp, _i32],
+    "qd_set_amplitudes": [_vp, _vp, _i32],
+    "qd_sync": [_vp, _i32p],
+}
+
+
+def exported_names() -> list[str]:
+    return list(_SIGS) + ["qd_strerror", "qd_last_error"]
+
+
+def load(path: Optional[str] = None):
+    """Load libqudit.so (raises if it is not built)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise QuditError(-5, f"libqudit.so is not built at {p}; run __graft_entry__.build()")
+    L = ctypes.CDLL(p)
+    for name, args in _SIGS.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    L.qd_strerror.argtypes = [ctypes.c_int]
+    L.qd_strerror.restype = ctypes.c_char_p
+    L.qd_last_error.argtypes = []
+    L.qd_last_error.restype = ctypes.c_char_p
+    if path is None:
+        _lib = L
+    return L
+
+
+def _check(rc: int):
+    if rc != QD_OK:
+        raise QuditError(rc, load().qd_last_error().decode(errors="replace"))
+
+
+def _arr_i32(xs):
+    a = np.ascontiguousarray(np.asarray(list(xs), dtype=np.int32))
+    return a, (a.ctypes.data_as(_i32p) if a.size else None)
+
+
+def _cplx(m) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(m, dtype=np.complex128))
+
+
+# ---- register ------------------------------------------------------------
+
+def qd_create(dims: Sequence[int], init_levels: Optional[Sequence[int]] = None, precision: int = QD_C64,
+              dev_buf: int = 0, dev_buf_bytes: int = 0, stream: int = 0) -> int:
+    d, dp = _arr_i32(dims)
+    lv, lp = _arr_i32(init_levels) if init_levels is not None else (None, None)
+    out = _vp()
+    _check(load().qd_create(dp, len(d), lp, precision, _vp(dev_buf or None), dev_buf_bytes, _vp(stream or None),
+                            ctypes.byref(out)))
+    return out.value
+
+
+def qd_destroy(reg: int) -> None:
+    _check(load().qd_destroy(_vp(reg)))
+
+
+def qd_reset(reg: int, init_levels: Optional[Sequence[int]] = None) -> None:
+    lv, lp = _arr_i32(init_levels) if init_levels is not None else (None, None)
+    _check(load().qd_reset(_vp(reg), lp))
+
+
+def qd_info(reg: int) -> dict:
+    N, n, st, pr = _i64(), _i32(), _vp(), _i32()
+    _check(load().qd_info(_vp(reg), ctypes.byref(N), ctypes.byref(n), ctypes.byref(st), ctypes.byref(pr)))
+    return {"N": N.value, "n": n.value, "state": st.value, "precision": pr.value}
+
+
+def qd_set_stream(reg: int, stream: int) -> None:
+    _check(load().qd_set_stream(_vp(reg), _vp(stream or None)))
+
+
+# ---- gates ------------------------------------------------------------------
+
+def qd_apply(reg: int, matrix, targets, controls=(), ctrl_levels=None) -> None:
+    m = _cplx(matrix)
+    t, tp = _arr_i32(targets)
+    c, cp = _arr_i32(controls)
+    lv, lp = _arr_i32(ctrl_levels) if ctrl_levels is not None else (None, None)
+    _check(load().qd_apply(_vp(reg), m.ctypes.data_as(_dp), tp, len(t), cp, lp, len(c)))
+
+
+def qd_apply_diag(reg: int, diag, targets, controls=(), ctrl_levels=None) -> None:
+    m = _cplx(diag)
+    t, tp = _arr_i32(targets)
+    c, cp = _arr_i32(controls)
+    lv, lp = _arr_i32(ctrl_levels) if ctrl_levels is not None else (None, None)
+    _check(load().qd_apply_diag(_vp(reg), m.ctypes.data_as(_dp), tp, len(t), cp, lp, len(c)))
+
+
+def qd_apply_x(reg: int, t: int, shift: int = 1) -> None:
+    _check(load().qd_apply_x(_vp(reg), t, shift))
+
+
+def qd_apply_z(reg: int, t: int, power: int = 1) -> None:
+    _check(load().qd_apply_z(_vp(reg), t, power))
+
+
+def qd_apply_h(reg: int, t: int) -> None:
+    _check(load().qd_apply_h(_vp(reg), t))
+
+
+def qd_apply_cx(reg: int, c: int, t: int, shift: int = 1, ctrl_level: int = -1) -> None:
+    _check(load().qd_apply_cx(_vp(reg), c, t, shift, ctrl_level))
+
+
+def qd_apply_mct(reg: int, controls, t: int, shift: int = 1, ctrl_levels=None) -> None:
+    c, cp = _arr_i32(controls)
+    lv, lp = _arr_i32(ctrl_levels) if ctrl_levels is not None else (None, None)
+    _check(load().qd_apply_mct(_vp(reg), cp, lp, len(c), t, shift))
+
+
+_KIND = {"X": QD_GATE_X, "Z": QD_GATE_Z, "H": QD_GATE_H, "U": QD_GATE_U, "DIAG": QD_GATE_DIAG}
+
+
+class GateArray:
+    """A C array of qd_gate built from gate records (objects with ``kind``,
+    ``targets``, ``controls``, ``levels``, ``param``, ``matrix``); it keeps
+    the matrix buffers alive while the array is in use."""
+
+    def __init__(self, gates):
+        self.n = len(gates)
+        self.arr = (QdGate * max(1, self.n))()
+        self._keep = []
+        for i, g in enumerate(gates):
+            s = self.arr[i]
+            s.kind = _KIND[g.kind]
+            s.k = len(g.targets)
+            for j, t in enumerate(g.targets):
+                s.targets[j] = int(t)
+            ctrls = tuple(g.controls or ())
+            s.nc = len(ctrls)
+            lv = g.levels if g.levels is not None else [-1] * len(ctrls)
+            for j, (c, l) in enumerate(zip(ctrls, lv)):
+                s.controls[j] = int(c)
+                s.ctrl_levels[j] = -1 if l is None else int(l)
+            s.param = int(g.param or 0)
+            if g.matrix is not None:
+                m = _cplx(g.matrix)
+                self._keep.append(m)
+                s.matrix = m.ctypes.data_as(_dp)
+            else:
+                s.matrix = None
+        self.ptr = ctypes.cast(self.arr, ctypes.POINTER(QdGate))
+
+    def matrix_bytes(self) -> int:
+        return int(sum(m.nbytes for m in self._keep))
+
+
+def qd_apply_gate(reg: int, gate) -> None:
+    ga = GateArray([gate])
+    _check(load().qd_apply_gate(_vp(reg), ga.ptr))
+
+
+def qd_plan_create(reg: int, gates, plan_kind: int = QD_PLAN_NONE) -> int:
+    ga = gates if isinstance(gates, GateArray) else GateArray(gates)
+    out = _vp()
+    _check(load().qd_plan_create(_vp(reg), ga.ptr, ga.n, plan_kind, ctypes.byref(out)))
+    return out.value
+
+
+def qd_plan_run(plan: int) -> None:
+    _check(load().qd_plan_run(_vp(plan)))
+
+
+def qd_plan_info(plan: int) -> dict:
+    la, bl = _i32(), _i32()
+    _check(load().qd_plan_info(_vp(plan), ctypes.byref(la), ctypes.byref(bl)))
+    return {"launches": la.value, "blocks": bl.value}
+
+
+def qd_plan_profile(plan: int, enable: bool = True) -> None:
+    _check(load().qd_plan_profile(_vp(plan), 1 if enable else 0))
+
+
+KCLASS_NAMES = {0: "dense_direct", 1: "dense_tile", 2: "mono_direct", 3: "mono_tile"}
+
+
+def qd_plan_timings(plan: int, with_times: bool = True):
+    """(ms[launches] or None, alg_bytes[launches], kclass[launches])."""
+    n = qd_plan_info(plan)["launches"]
+    ms = np.zeros(max(n, 1), dtype=np.float32)
+    ab = np.zeros(max(n, 1), dtype=np.float64)
+    kc = np.zeros(max(n, 1), dtype=np.int32)
+    _check(load().qd_plan_timings(_vp(plan), ms.ctypes.data_as(ctypes.POINTER(ctypes.c_float)) if with_times else None,
+                                  ab.ctypes.data_as(_dp), kc.ctypes.data_as(_i32p)))
+    return (ms[:n] if with_times else None), ab[:n], kc[:n]
+
+
+def kclass_name(c: int) -> str:
+    return f"{KCLASS_NAMES[c & 0xff]}_D{c >> 8}"
+
+
+def qd_plan_destroy(plan: int) -> None:
+    _check(load().qd_plan_destroy(_vp(plan)))
+
+
+def qd_run_circuit(reg: int, gates, plan_kind: int = QD_PLAN_NONE) -> None:
+    ga = gates if isinstance(gates, GateArray) else GateArray(gates)
+    _check(load().qd_run_circuit(_vp(reg), ga.ptr, ga.n, plan_kind))
+
+
+# ---- readout -----------------------------------------------------------------
+
+def qd_norm(reg: int) -> float:
+    out = ctypes.c_double()
+    _check(load().qd_norm(_vp(reg), ctypes.byref(out)))
+    return out.value
+
+
+def _n(reg):
+    return qd_info(reg)["N"]
+
+
+def qd_probabilities(reg: int, out: Optional[np.ndarray] = None, where: int = QD_HOST, dev_ptr: int = 0):
+    if where == QD_DEVICE:
+        _check(load().qd_probabilities(_vp(reg), ctypes.cast(_vp(dev_ptr), _dp), QD_DEVICE))
+        return None
+    if out is None:
+        out = np.empty(_n(reg), dtype=np.float64)
+    _check(load().qd_probabilities(_vp(reg), out.ctypes.data_as(_dp), QD_HOST))
+    return out
+
+
+def qd_marginal(reg: int, q: int, d: int) -> np.ndarray:
+    out = np.empty(d, dtype=np.float64)
+    _check(load().qd_marginal(_vp(reg), q, out.ctypes.data_as(_dp)))
+    return out
+
+
+def qd_cdf(reg: int, out: Optional[np.ndarray] = None) -> np.ndarray:
+    if out is None:
+        out = np.empty(_n(reg), dtype=np.float64)
+    _check(load().qd_cdf(_vp(reg), out.ctypes.data_as(_dp), QD_HOST))
+    return out
+
+
+def qd_sample(reg: int, seed: int, shots: int) -> np.ndarray:
+    out = np.empty(shots, dtype=np.int64)
+    _check(load().qd_sample(_vp(reg), ctypes.c_uint64(seed), shots, out.ctypes.data_as(_i64p)))
+    return out
+
+
+def qd_sample_u(reg: int, u) -> np.ndarray:
+    u = np.ascontiguousarray(np.asarray(u, dtype=np.float64))
+    out = np.empty(len(u), dtype=np.int64)
+    _check(load().qd_sample_u(_vp(reg), u.ctypes.data_as(_dp), len(u), out.ctypes.data_as(_i64p)))
+    return out
+
+
+def qd_get_amplitudes(reg: int, out: Optional[np.ndarray] = None) -> np.ndarray:
+    info = qd_info(reg)
+    dt = np.complex64 if info["precision"] == QD_C64 else np.complex128
+    if out is None:
+        out = np.empty(info["N"], dtype=dt)
+    assert out.dtype == dt and out.size == info["N"] and out.flags.c_contiguous
+    _check(load().qd_get_amplitudes(_vp(reg), _vp(out.ctypes.data), QD_HOST))
+    return out
+
+
+def qd_set_amplitudes(reg: int, src, where: int = QD_HOST) -> None:
+    if where == QD_DEVICE:
+        _check(load().qd_set_amplitudes(_vp(reg), _vp(int(src)), QD_DEVICE))
+        return
+    info = qd_info(reg)
+    dt = np.complex64 if info["precision"] == QD_C64 else np.complex128
+    a = np.ascontiguousarray(np.asarray(src, dtype=dt))
+    assert a.size == info["N"]
+    _check(load().qd_set_amplitudes(_vp(reg), _vp(a.ctypes.data), QD_HOST))
+
+
+def qd_sync(reg: int) -> int:
+    err = _i32()
+    rc = load().qd_sync(_vp(reg), ctypes.byref(err))
+    _check(rc)
+    return err.value
+
+
+def qd_strerror(code: int) -> str:
+    return load().qd_strerror(code).decode()
+
+
+def qd_last_error() -> str:
+    return load().qd_last_error().decode(errors="replace")
+
+
+class Register:
+    """Owns one qd_reg handle (convenience wrapper, marshalling only)."""
+
+    def __init__(self, dims, init_levels=None, precision=QD_C64, dev_buf=0, dev_buf_bytes=0, stream=0):
+        self.dims = [int(d) for d in dims]
+        self.precision = precision
+        self.h = qd_create(self.dims, init_levels, precision, dev_buf, dev_buf_bytes, stream)
+
+    def close(self):
+        if self.h:
+            qd_destroy(self.h)
+            self.h = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, gates, plan_kind=QD_PLAN_NONE):
+        qd_run_circuit(self.h, gates, plan_kind)
+
+    def amplitudes(self):
+        return qd_get_amplitudes(self.h)
+
+
+# ---- host-only planner inspection (include/qudit_debug.h) ------------------
+
+def qd_debug_gate_members(dims: Sequence[int], gate, cap: int = 1 << 20):
+    """Replay the planned kernel's index arithmetic on the host.
+
+    Returns (members[groups, D] int64, info dict); see include/qudit_debug.h."""
+    L = load()
+    fn = L.qd_debug_gate_members
+    fn.argtypes = [_i32p, _i32, ctypes.POINTER(QdGate), _i64p, _i64, _i64p]
+    fn.restype = ctypes.c_int
+    d, dp = _arr_i32(dims)
+    ga = GateArray([gate])
+    out = np.zeros(cap, dtype=np.int64)
+    info = np.zeros(7, dtype=np.int64)
+    _check(fn(dp, len(d), ga.ptr, out.ctypes.data_as(_i64p), cap, info.ctypes.data_as(_i64p)))
+    keys = ["mode", "D", "groups", "kind", "active", "B", "noop"]
+    inf = {k: int(v) for k, v in zip(keys, info)}
+    if inf["noop"]:
+        return np.zeros((0, 0), dtype=np.int64), inf
+    n = inf["groups"] * inf["D"]
+    assert n <= cap
+    return out[:n].reshape(inf["groups"], inf["D"]), inf
