@@ -122,6 +122,14 @@ int qd_info(const qd_reg *reg, int64_t *num_amplitudes, int32_t *n, void **state
 /* Move subsequent work of the register to another stream. */
 int qd_set_stream(qd_reg *reg, void *stream);
 
+/* Launch-shape tuning of later gate plans on this register.
+ * QD_TUNE_TILE_STRIDE: gates whose lowest target or control stride (in
+ * amplitudes) is below value are staged through shared memory ("tile"
+ * kernels); 0 never tiles.  Default: environment QD_TILE_STRIDE, else 0.
+ * Errors: QD_ERR_ARG for an unknown key or a negative value. */
+#define QD_TUNE_TILE_STRIDE 1
+int qd_set_tuning(qd_reg *reg, int32_t key, int64_t value);
+
 /* ---- gate application, in place (Sec. 2.1.2, Sec. 3.4) ---------------- */
 
 /* Apply a dense D x D matrix to targets[0..k) under controls[0..nc) at
@@ -166,8 +174,9 @@ int qd_plan_run(qd_plan *plan);
 /* Number of kernel launches one run enqueues, and of fused blocks. */
 int qd_plan_info(const qd_plan *plan, int32_t *launches, int32_t *blocks);
 int qd_plan_destroy(qd_plan *plan);
-/* Per-launch timing: with enable != 0 every qd_plan_run records a CUDA
- * event before each launch and after the last one on the register's stream.
+/* Per-launch timing: with enable != 0 every qd_plan_run launches directly
+ * (no graph), holds the stream with a host function until all launches are
+ * enqueued, and records a CUDA event before each launch and after the last.
  * qd_plan_timings then synchronises the stream and writes, for launch i of
  * the latest run, its device time in ms (events), its algorithmic HBM bytes
  * (2 x bytes of the amplitudes it reads and writes) and its kernel class

@@ -24,6 +24,9 @@ extern "C" {
 #endif
 int qd_debug_gate_members(const int32_t *dims, int32_t n, const qd_gate *gate, int64_t *out, int64_t cap,
                           int64_t *info);
+/* The same with an explicit tile-stride threshold (see QD_TUNE_TILE_STRIDE). */
+int qd_debug_gate_members_tuned(const int32_t *dims, int32_t n, const qd_gate *gate, int64_t tile_stride,
+                                int64_t *out, int64_t cap, int64_t *info);
 #ifdef __cplusplus
 }
 #endif

@@ -7,8 +7,12 @@
 // Registers follow Sec. 2.2 / Sec. 3.2: N = prod d_q, qudit 0 least
 // significant, initial basis levels.
 #include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <thread>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -63,6 +67,7 @@ struct qd_reg {
     double *cdf = nullptr;  // lazily allocated N doubles
     double *cdf_chunks = nullptr;
     int32_t *dev_err = nullptr;
+    int64_t tile_stride = -1;  // -1: process default
 };
 
 struct qd_plan {
@@ -72,8 +77,8 @@ struct qd_plan {
     bool profile = false;
     std::vector<cudaEvent_t> events;  // launches + 1 when profiling
     bool use_graph = true;            // capture on first run, replay afterwards
+    std::atomic<int> gate_open{1};    // profiling: holds the stream until every launch is enqueued
     cudaGraphExec_t exec = nullptr;   // captured launches (non-default streams)
-    bool exec_profiled = false;
     void drop_graph() {
         if (exec) cudaGraphExecDestroy(exec);
         exec = nullptr;
@@ -252,6 +257,7 @@ int plan_gate(const qd_reg *r, const double *M, const Acting &a, bool diag_only,
     g = GatePlan{};
     const int D = a.D;
     g.D = D;
+    g.N = (uint64_t)r->N;
     // matrix / classification
     if (diag_only) {
         for (int i = 0; i < D; ++i) {
@@ -308,7 +314,12 @@ int plan_gate(const qd_reg *r, const double *M, const Acting &a, bool diag_only,
     if (g.kind == Kind::Dense) g.alg_bytes = 2.0 * (double)touched * (double)r->esize;
     else g.alg_bytes = 2.0 * (double)(touched / D) * __builtin_popcount(g.active) * (double)r->esize;
 
-    if (min_stride >= kLowStride) {
+    static const int64_t default_low_stride = [] {
+        const char *v = std::getenv("QD_TILE_STRIDE");
+        return v ? (int64_t)std::atoll(v) : kLowStride;
+    }();
+    const int64_t low_stride = r->tile_stride >= 0 ? r->tile_stride : default_low_stride;
+    if (min_stride >= low_stride) {
         g.mode = Mode::Direct;
         g.R = (uint64_t)(r->N / (D * cprod));
         std::vector<std::pair<int64_t, int64_t>> ins;
@@ -327,7 +338,7 @@ int plan_gate(const qd_reg *r, const double *M, const Acting &a, bool diag_only,
     g.mode = Mode::Tile;
     int m = 0;
     for (int q = 0; q < n; ++q)
-        if ((is_t[q] || is_c[q]) && s[q] < kLowStride) m = q + 1;
+        if ((is_t[q] || is_c[q]) && s[q] < low_stride) m = q + 1;
     auto DH_of = [&](int mm) {
         int64_t dh = 1;
         for (int q = mm; q < n; ++q)
@@ -672,6 +683,13 @@ int qd_set_stream(qd_reg *r, void *stream) {
     return QD_OK;
 }
 
+int qd_set_tuning(qd_reg *r, int32_t key, int64_t value) {
+    if (int rc = reg_ok(r)) return rc;
+    if (key != QD_TUNE_TILE_STRIDE || value < 0) return fail(QD_ERR_ARG, "unknown tuning key or negative value");
+    r->tile_stride = value;
+    return QD_OK;
+}
+
 int qd_apply(qd_reg *r, const double *matrix, const int32_t *targets, int32_t k, const int32_t *controls,
              const int32_t *ctrl_levels, int32_t nc) {
     if (int rc = reg_ok(r)) return rc;
@@ -769,15 +787,35 @@ cudaError_t enqueue_plan(qd_plan *p, cudaStream_t s) {
 }
 }  // namespace
 
+namespace {
+// Host function that holds the stream until the enqueueing thread has
+// submitted the whole profiled run (bounded: gives up after ~2 s), so the
+// per-launch events measure back-to-back kernels, not host submission.
+void CUDART_CB hold_until_open(void *arg) {
+    auto *flag = static_cast<std::atomic<int> *>(arg);
+    for (int i = 0; i < 200000 && flag->load(std::memory_order_acquire) == 0; ++i)
+        std::this_thread::sleep_for(std::chrono::microseconds(10));
+}
+}  // namespace
+
 int qd_plan_run(qd_plan *p) {
     if (!p) return fail(QD_ERR_ARG, "null plan");
     cudaStream_t s = p->reg->stream;
+    if (p->profile) {  // events cannot be timed inside a graph: direct launches behind a hold
+        QD_CUDA(cudaStreamSynchronize(s));
+        p->gate_open.store(0, std::memory_order_release);
+        cudaError_t e = cudaLaunchHostFunc(s, hold_until_open, &p->gate_open);
+        if (e == cudaSuccess) e = enqueue_plan(p, s);
+        p->gate_open.store(1, std::memory_order_release);
+        if (e != cudaSuccess) return cuda_fail(e, "profiled launch");
+        return QD_OK;
+    }
     if (!s || !p->use_graph) {  // the legacy default stream cannot be captured: launch directly
         cudaError_t e = enqueue_plan(p, s);
         if (e != cudaSuccess) return cuda_fail(e, "gate launch");
         return QD_OK;
     }
-    if (!p->exec || p->exec_profiled != p->profile) {
+    if (!p->exec) {
         p->drop_graph();
         QD_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
         cudaError_t e = enqueue_plan(p, s);
@@ -794,7 +832,6 @@ int qd_plan_run(qd_plan *p) {
             p->exec = nullptr;
             return cuda_fail(e, "graph instantiate");
         }
-        p->exec_profiled = p->profile;
     }
     QD_CUDA(cudaGraphLaunch(p->exec, s));
     return QD_OK;
@@ -974,6 +1011,11 @@ int qd_sync(qd_reg *r, int32_t *device_error) {
 
 int qd_debug_gate_members(const int32_t *dims, int32_t n, const qd_gate *gate, int64_t *out, int64_t cap,
                           int64_t *info) {
+    return qd_debug_gate_members_tuned(dims, n, gate, -1, out, cap, info);
+}
+
+int qd_debug_gate_members_tuned(const int32_t *dims, int32_t n, const qd_gate *gate, int64_t tile_stride,
+                                int64_t *out, int64_t cap, int64_t *info) {
     if (!dims || n < 1 || n > QD_MAX_QUDITS || !info) return fail(QD_ERR_ARG, "bad arguments");
     qd_reg r;
     r.n = n;
@@ -987,6 +1029,7 @@ int qd_debug_gate_members(const int32_t *dims, int32_t n, const qd_gate *gate, i
     r.s[n] = s;
     r.N = s;
     r.esize = 8;
+    r.tile_stride = tile_stride;
     GatePlan g;
     bool noop = false;
     int rc = prepare_gate(&r, gate, g, &noop);

@@ -1,5 +1,6 @@
 // Per-gate in-place apply kernels (QuDiet Sec. 2.1.2 gates, Sec. 3.4 user
-// gates), instantiated for FP32 (complex64) and FP64 (complex128) states.
+// gates), instantiated for FP32 (complex64) and FP64 (complex128) states and
+// for 32- or 64-bit index arithmetic.
 //
 // A gate with targets T (D = prod d_t local states) and controls C at levels
 // l_c maps, for every group r over the remaining qudits, the D amplitudes
@@ -9,15 +10,17 @@
 // touched.
 //
 // Two memory schemes:
-//   direct  one thread per group, loads straight from HBM.  Used when every
-//           target and control has a flat stride >= 32, so that a warp's 32
-//           consecutive groups read 32 consecutive amplitudes per member.
+//   direct  one thread per group, loads straight from global memory.  Used
+//           when every target and control has a flat stride >= the planner's
+//           threshold, so that a warp's 32 consecutive groups read runs of
+//           consecutive amplitudes for each member.
 //   tile    a CTA stages DH chunks of B contiguous amplitudes (B = s_m covers
 //           all low-stride targets and controls) in shared memory with
-//           coalesced loads, applies the gate to the groups inside the tile,
-//           and writes the chunks back.
+//           asynchronous copies, applies the gate to the groups inside the
+//           tile, and writes the chunks back with coalesced stores.
 #pragma once
 #include <algorithm>
+#include <type_traits>
 
 #include "qd_plan.h"
 
@@ -39,126 +42,218 @@ __device__ __forceinline__ v2<T> cmul(const v2<T> u, const v2<T> v) {
     return r;
 }
 
-// ------------------------------------------------------------ argument blocks
-// MD is the compile-time member bound; EX says D == MD exactly.
+// complex64 states carry every gate coefficient as an unevaluated pair of
+// floats c = hi + lo (|lo| <= ulp(hi)/2).  Rounding the coefficients to one
+// float would make the applied matrix non-unitary by ~1e-7 in the same way
+// for every group of the register, a coherent norm drift that adds up over a
+// circuit; with the pair the coefficient error is ~1e-14 and what remains is
+// the incoherent per-amplitude rounding of FP32 arithmetic.
+template <typename T> constexpr bool kSplit = std::is_same<T, float>::value;
+template <typename T> __host__ __device__ constexpr int split_len(int n) { return kSplit<T> ? n : 1; }
 
-template <typename T, int MD>
+template <typename T>
+__device__ __forceinline__ v2<T> cmul_split(const v2<T> hi, const v2<T> lo, const v2<T> v) {
+    if constexpr (kSplit<T>) {
+        v2<T> r = cmul<T>(lo, v);
+        r.x = fma(hi.x, v.x, fma(-hi.y, v.y, r.x));
+        r.y = fma(hi.x, v.y, fma(hi.y, v.x, r.y));
+        return r;
+    } else {
+        return cmul<T>(hi, v);
+    }
+}
+
+template <typename T>
+inline void split_coef(double re, double im, v2<T> &hi, v2<T> &lo) {
+    hi = mk<T>((T)re, (T)im);
+    lo = mk<T>((T)(re - (double)hi.x), (T)(im - (double)hi.y));
+}
+
+template <typename I> using ExpandT = typename ExpandOf<I>::type;
+
+// ------------------------------------------------------------ argument blocks
+// MD is the compile-time member bound; EX says D == MD exactly; I is the index
+// type.
+
+template <typename T, typename I, int MD>
 struct DenseDirectArgs {
     v2<T> *psi;
-    uint64_t R, base;
+    I R, base;
     int32_t D;
-    Expand64 ex;
-    int64_t off[MD];
+    ExpandT<I> ex;
+    I off[MD];
     v2<T> U[MD * MD];  // row-major, zero-padded to MD x MD
+    v2<T> Ulo[split_len<T>(MD * MD)];
 };
 
-template <typename T, int MD>
+template <typename T, typename I, int MD>
 struct MonoDirectArgs {
     v2<T> *psi;
-    uint64_t R, base;
+    I R, base;
     uint32_t active, unit;
-    Expand64 ex;
-    int64_t off[MD];     // destination offsets
-    int64_t offsrc[MD];  // off[src[i]]
+    ExpandT<I> ex;
+    I off[MD];     // destination offsets
+    I offsrc[MD];  // off[src[i]]
     v2<T> lam[MD];
+    v2<T> lamlo[split_len<T>(MD)];
 };
 
+template <typename I>
 struct TileGeo {
-    uint64_t R_tiles, base_hi;
+    I R_tiles, base_hi;
     uint32_t B, DH, tpc, G_in, lo_off, pad;
     FastDiv32 divB, divG;
-    Expand64 ex_hi;
+    ExpandT<I> ex_hi;
     Expand32 ex_lo;
 };
 
-template <typename T, int MD>
+template <typename T, typename I, int MD>
 struct DenseTileArgs {
     v2<T> *psi;
     int32_t D;
-    TileGeo t;
-    int64_t offH[MD];
+    TileGeo<I> t;
+    I offH[MD];
     int32_t smoff[MD];
     v2<T> U[MD * MD];
+    v2<T> Ulo[split_len<T>(MD * MD)];
 };
 
-template <typename T, int MD>
+template <typename T, typename I, int MD>
 struct MonoTileArgs {
     v2<T> *psi;
     uint32_t active, unit;
-    TileGeo t;
-    int64_t offH[MD];
+    TileGeo<I> t;
+    I offH[MD];
     int32_t smoff[MD];
     int32_t smoffsrc[MD];
     v2<T> lam[MD];
+    v2<T> lamlo[split_len<T>(MD)];
 };
 
 // ------------------------------------------------------------ direct kernels
 
-template <typename T, int MD, bool EX>
-__global__ void __launch_bounds__(256) k_dense_direct(const __grid_constant__ DenseDirectArgs<T, MD> a) {
+// Groups per thread per iteration: loads of all of them are issued before any
+// arithmetic, for memory-level parallelism (bounded by register pressure).
+template <typename T, typename I, int MD>
+__host__ __device__ constexpr int direct_unroll() {
+    return (MD * (int)sizeof(v2<T>)) <= 32 && sizeof(I) == 4 ? 2 : 1;
+}
+
+template <typename T, typename I, int MD, bool EX>
+__global__ void __launch_bounds__(256) k_dense_direct(const __grid_constant__ DenseDirectArgs<T, I, MD> a) {
+    constexpr int UN = direct_unroll<T, I, MD>();
     const int D = EX ? MD : a.D;
-    const uint64_t step = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < a.R; r += step) {
-        const uint64_t base = expand(r, a.ex) + a.base;
-        v2<T> v[MD];
+    const I step = (I)gridDim.x * blockDim.x;
+    for (I r0 = (I)blockIdx.x * blockDim.x + threadIdx.x; r0 < a.R; r0 += UN * step) {
+        I base[UN];
+        bool ok[UN];
+        v2<T> v[UN][MD];
 #pragma unroll
-        for (int j = 0; j < MD; ++j) v[j] = (EX || j < D) ? a.psi[base + a.off[j]] : mk<T>(T(0), T(0));
+        for (int u = 0; u < UN; ++u) {
+            const I r = r0 + u * step;
+            ok[u] = r < a.R;
+            base[u] = ok[u] ? expand(r, a.ex) + a.base : 0;
+        }
 #pragma unroll
-        for (int i = 0; i < MD; ++i) {
-            if (EX || i < D) {
-                v2<T> acc = mk<T>(T(0), T(0));
+        for (int u = 0; u < UN; ++u)
 #pragma unroll
-                for (int j = 0; j < MD; ++j) cmac<T>(acc, a.U[i * MD + j], v[j]);
-                a.psi[base + a.off[i]] = acc;
+            for (int j = 0; j < MD; ++j)
+                v[u][j] = (ok[u] && (EX || j < D)) ? a.psi[base[u] + a.off[j]] : mk<T>(T(0), T(0));
+#pragma unroll
+        for (int u = 0; u < UN; ++u) {
+            if (!ok[u]) continue;
+#pragma unroll
+            for (int i = 0; i < MD; ++i) {
+                if (EX || i < D) {
+                    v2<T> acc = mk<T>(T(0), T(0));
+                    if constexpr (kSplit<T>) {
+#pragma unroll
+                        for (int j = 0; j < MD; ++j) cmac<T>(acc, a.Ulo[i * MD + j], v[u][j]);
+                    }
+#pragma unroll
+                    for (int j = 0; j < MD; ++j) cmac<T>(acc, a.U[i * MD + j], v[u][j]);
+                    a.psi[base[u] + a.off[i]] = acc;
+                }
             }
         }
     }
 }
 
-template <typename T, int MD>
-__global__ void __launch_bounds__(256) k_mono_direct(const __grid_constant__ MonoDirectArgs<T, MD> a) {
-    const uint64_t step = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < a.R; r += step) {
-        const uint64_t base = expand(r, a.ex) + a.base;
-        v2<T> w[MD];
+template <typename T, typename I, int MD>
+__global__ void __launch_bounds__(256) k_mono_direct(const __grid_constant__ MonoDirectArgs<T, I, MD> a) {
+    constexpr int UN = direct_unroll<T, I, MD>();
+    const I step = (I)gridDim.x * blockDim.x;
+    for (I r0 = (I)blockIdx.x * blockDim.x + threadIdx.x; r0 < a.R; r0 += UN * step) {
+        I base[UN];
+        bool ok[UN];
+        v2<T> w[UN][MD];
 #pragma unroll
-        for (int i = 0; i < MD; ++i)
-            if ((a.active >> i) & 1u) w[i] = a.psi[base + a.offsrc[i]];
+        for (int u = 0; u < UN; ++u) {
+            const I r = r0 + u * step;
+            ok[u] = r < a.R;
+            base[u] = ok[u] ? expand(r, a.ex) + a.base : 0;
+        }
 #pragma unroll
-        for (int i = 0; i < MD; ++i)
-            if ((a.active >> i) & 1u) a.psi[base + a.off[i]] = ((a.unit >> i) & 1u) ? w[i] : cmul<T>(a.lam[i], w[i]);
+        for (int u = 0; u < UN; ++u)
+#pragma unroll
+            for (int i = 0; i < MD; ++i)
+                if (ok[u] && ((a.active >> i) & 1u)) w[u][i] = a.psi[base[u] + a.offsrc[i]];
+#pragma unroll
+        for (int u = 0; u < UN; ++u)
+#pragma unroll
+            for (int i = 0; i < MD; ++i)
+                if (ok[u] && ((a.active >> i) & 1u))
+                    a.psi[base[u] + a.off[i]] =
+                        ((a.unit >> i) & 1u) ? w[u][i] : cmul_split<T>(a.lam[i], a.lamlo[kSplit<T> ? i : 0], w[u][i]);
     }
 }
 
 // -------------------------------------------------------------- tile kernels
 
-// Dynamic shared memory: chunk bases (uint64, tpc*DH) then the tile data.
-template <typename T>
+// Dynamic shared memory: chunk bases (I, tpc*DH entries) then the tile data.
+template <typename T, typename I>
 __device__ __forceinline__ v2<T> *tile_data(unsigned char *raw, uint32_t nchunks) {
-    size_t off = ((size_t)nchunks * sizeof(uint64_t) + 15) & ~size_t(15);
+    size_t off = ((size_t)nchunks * sizeof(I) + 15) & ~size_t(15);
     return reinterpret_cast<v2<T> *>(raw + off);
 }
 
-template <typename T, int MD>
-__device__ __forceinline__ void tile_load(const TileGeo &t, const int64_t *offH, v2<T> *psi, uint64_t tile0,
-                                          uint32_t nt, uint64_t *cbase, v2<T> *sm) {
+// Asynchronous global->shared copy of one amplitude (sm_80+ cp.async; 8-byte
+// copies go through L1, 16-byte copies bypass it).
+template <typename T>
+__device__ __forceinline__ void cp_async_amp(v2<T> *dst, const v2<T> *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    if constexpr (sizeof(v2<T>) == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+template <typename T, typename I, int MD>
+__device__ __forceinline__ void tile_load(const TileGeo<I> &t, const I *offH, v2<T> *psi, I tile0, uint32_t nt,
+                                          I *cbase, v2<T> *sm) {
     const uint32_t nch = nt * t.DH;
     for (uint32_t c = threadIdx.x; c < nch; c += blockDim.x) {
         const uint32_t u = c / t.DH;
         const uint32_t h = c - u * t.DH;
-        cbase[c] = expand(tile0 + u, t.ex_hi) * t.B + t.base_hi + offH[h];
+        cbase[c] = expand((I)(tile0 + u), t.ex_hi) * t.B + t.base_hi + offH[h];
     }
     __syncthreads();
     const uint32_t E = nch * t.B;
     for (uint32_t f = threadIdx.x; f < E; f += blockDim.x) {
         const uint32_t c = fdiv(f, t.divB);
-        sm[f] = psi[cbase[c] + (f - c * t.B)];
+        cp_async_amp<T>(sm + f, psi + cbase[c] + (f - c * t.B));
     }
+    cp_async_wait_all();
     __syncthreads();
 }
 
-template <typename T>
-__device__ __forceinline__ void tile_store(const TileGeo &t, v2<T> *psi, uint32_t nt, const uint64_t *cbase,
+template <typename T, typename I>
+__device__ __forceinline__ void tile_store(const TileGeo<I> &t, v2<T> *psi, uint32_t nt, const I *cbase,
                                            const v2<T> *sm) {
     const uint32_t E = nt * t.DH * t.B;
     for (uint32_t f = threadIdx.x; f < E; f += blockDim.x) {
@@ -167,18 +262,18 @@ __device__ __forceinline__ void tile_store(const TileGeo &t, v2<T> *psi, uint32_
     }
 }
 
-template <typename T, int MD, bool EX>
-__global__ void __launch_bounds__(256) k_dense_tile(const __grid_constant__ DenseTileArgs<T, MD> a) {
+template <typename T, typename I, int MD, bool EX>
+__global__ void __launch_bounds__(256) k_dense_tile(const __grid_constant__ DenseTileArgs<T, I, MD> a) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    const TileGeo &t = a.t;
+    const TileGeo<I> &t = a.t;
     const int D = EX ? MD : a.D;
-    uint64_t *cbase = reinterpret_cast<uint64_t *>(smraw);
-    v2<T> *sm = tile_data<T>(smraw, t.tpc * t.DH);
+    I *cbase = reinterpret_cast<I *>(smraw);
+    v2<T> *sm = tile_data<T, I>(smraw, t.tpc * t.DH);
     const uint32_t tileE = t.DH * t.B;
-    for (uint64_t tile0 = (uint64_t)blockIdx.x * t.tpc; tile0 < t.R_tiles; tile0 += (uint64_t)gridDim.x * t.tpc) {
-        const uint64_t left = t.R_tiles - tile0;
-        const uint32_t nt = left < (uint64_t)t.tpc ? (uint32_t)left : t.tpc;
-        tile_load<T, MD>(t, a.offH, a.psi, tile0, nt, cbase, sm);
+    for (I tile0 = (I)blockIdx.x * t.tpc; tile0 < t.R_tiles; tile0 += (I)gridDim.x * t.tpc) {
+        const I left = t.R_tiles - tile0;
+        const uint32_t nt = left < (I)t.tpc ? (uint32_t)left : t.tpc;
+        tile_load<T, I, MD>(t, a.offH, a.psi, tile0, nt, cbase, sm);
         const uint32_t G = nt * t.G_in;
         for (uint32_t gi = threadIdx.x; gi < G; gi += blockDim.x) {
             const uint32_t u = fdiv(gi, t.divG);
@@ -190,6 +285,10 @@ __global__ void __launch_bounds__(256) k_dense_tile(const __grid_constant__ Dens
             for (int i = 0; i < MD; ++i) {
                 if (EX || i < D) {
                     v2<T> acc = mk<T>(T(0), T(0));
+                    if constexpr (kSplit<T>) {
+#pragma unroll
+                        for (int j = 0; j < MD; ++j) cmac<T>(acc, a.Ulo[i * MD + j], v[j]);
+                    }
 #pragma unroll
                     for (int j = 0; j < MD; ++j) cmac<T>(acc, a.U[i * MD + j], v[j]);
                     sm[eb + a.smoff[i]] = acc;
@@ -197,22 +296,22 @@ __global__ void __launch_bounds__(256) k_dense_tile(const __grid_constant__ Dens
             }
         }
         __syncthreads();
-        tile_store<T>(t, a.psi, nt, cbase, sm);
+        tile_store<T, I>(t, a.psi, nt, cbase, sm);
         __syncthreads();
     }
 }
 
-template <typename T, int MD>
-__global__ void __launch_bounds__(256) k_mono_tile(const __grid_constant__ MonoTileArgs<T, MD> a) {
+template <typename T, typename I, int MD>
+__global__ void __launch_bounds__(256) k_mono_tile(const __grid_constant__ MonoTileArgs<T, I, MD> a) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    const TileGeo &t = a.t;
-    uint64_t *cbase = reinterpret_cast<uint64_t *>(smraw);
-    v2<T> *sm = tile_data<T>(smraw, t.tpc * t.DH);
+    const TileGeo<I> &t = a.t;
+    I *cbase = reinterpret_cast<I *>(smraw);
+    v2<T> *sm = tile_data<T, I>(smraw, t.tpc * t.DH);
     const uint32_t tileE = t.DH * t.B;
-    for (uint64_t tile0 = (uint64_t)blockIdx.x * t.tpc; tile0 < t.R_tiles; tile0 += (uint64_t)gridDim.x * t.tpc) {
-        const uint64_t left = t.R_tiles - tile0;
-        const uint32_t nt = left < (uint64_t)t.tpc ? (uint32_t)left : t.tpc;
-        tile_load<T, MD>(t, a.offH, a.psi, tile0, nt, cbase, sm);
+    for (I tile0 = (I)blockIdx.x * t.tpc; tile0 < t.R_tiles; tile0 += (I)gridDim.x * t.tpc) {
+        const I left = t.R_tiles - tile0;
+        const uint32_t nt = left < (I)t.tpc ? (uint32_t)left : t.tpc;
+        tile_load<T, I, MD>(t, a.offH, a.psi, tile0, nt, cbase, sm);
         const uint32_t G = nt * t.G_in;
         for (uint32_t gi = threadIdx.x; gi < G; gi += blockDim.x) {
             const uint32_t u = fdiv(gi, t.divG);
@@ -223,10 +322,12 @@ __global__ void __launch_bounds__(256) k_mono_tile(const __grid_constant__ MonoT
                 if ((a.active >> i) & 1u) w[i] = sm[eb + a.smoffsrc[i]];
 #pragma unroll
             for (int i = 0; i < MD; ++i)
-                if ((a.active >> i) & 1u) sm[eb + a.smoff[i]] = ((a.unit >> i) & 1u) ? w[i] : cmul<T>(a.lam[i], w[i]);
+                if ((a.active >> i) & 1u)
+                    sm[eb + a.smoff[i]] =
+                        ((a.unit >> i) & 1u) ? w[i] : cmul_split<T>(a.lam[i], a.lamlo[kSplit<T> ? i : 0], w[i]);
         }
         __syncthreads();
-        tile_store<T>(t, a.psi, nt, cbase, sm);
+        tile_store<T, I>(t, a.psi, nt, cbase, sm);
         __syncthreads();
     }
 }
@@ -235,15 +336,22 @@ __global__ void __launch_bounds__(256) k_mono_tile(const __grid_constant__ MonoT
 
 int occupancy_blocks(const void *fn, int block, size_t smem);  // cached, in qd_api.cu
 
+template <typename I>
 inline size_t tile_smem_bytes(const GatePlan &g, size_t elem) {
     const size_t nch = (size_t)g.tpc * g.DH;
-    return ((nch * sizeof(uint64_t) + 15) & ~size_t(15)) + nch * g.B * elem;
+    return ((nch * sizeof(I) + 15) & ~size_t(15)) + nch * g.B * elem;
 }
 
-template <typename T>
-inline void fill_tilegeo(TileGeo &t, const GatePlan &g) {
-    t.R_tiles = g.R_tiles;
-    t.base_hi = g.base_off_hi;
+template <typename I>
+inline ExpandT<I> expand_for(const Expand64 &e) {
+    if constexpr (sizeof(I) == 4) return narrow(e);
+    else return e;
+}
+
+template <typename I>
+inline void fill_tilegeo(TileGeo<I> &t, const GatePlan &g) {
+    t.R_tiles = (I)g.R_tiles;
+    t.base_hi = (I)g.base_off_hi;
     t.B = g.B;
     t.DH = g.DH;
     t.tpc = g.tpc;
@@ -252,130 +360,153 @@ inline void fill_tilegeo(TileGeo &t, const GatePlan &g) {
     t.pad = 0;
     t.divB = g.divB;
     t.divG = g.divG;
-    t.ex_hi = g.ex_hi;
+    t.ex_hi = expand_for<I>(g.ex_hi);
     t.ex_lo = g.ex_lo;
 }
 
-template <typename T, int MD, bool EX>
+template <typename T, int MD>
+inline void fill_matrix(v2<T> *U, v2<T> *Ulo, const GatePlan &g) {
+    for (int i = 0; i < MD; ++i)
+        for (int j = 0; j < MD; ++j) {
+            v2<T> hi = mk<T>(T(0), T(0)), lo = hi;
+            if (i < g.D && j < g.D) split_coef<T>(g.U[2 * (i * g.D + j)], g.U[2 * (i * g.D + j) + 1], hi, lo);
+            U[i * MD + j] = hi;
+            if constexpr (kSplit<T>) Ulo[i * MD + j] = lo;
+        }
+    if constexpr (!kSplit<T>) Ulo[0] = mk<T>(T(0), T(0));
+}
+
+template <typename T, int MD>
+inline void fill_lam(v2<T> *lam, v2<T> *lamlo, const GatePlan &g) {
+    for (int i = 0; i < MD; ++i) {
+        v2<T> hi = mk<T>(T(1), T(0)), lo = mk<T>(T(0), T(0));
+        if (i < g.D) split_coef<T>(g.lam[2 * i], g.lam[2 * i + 1], hi, lo);
+        lam[i] = hi;
+        if constexpr (kSplit<T>) lamlo[i] = lo;
+    }
+    if constexpr (!kSplit<T>) lamlo[0] = mk<T>(T(0), T(0));
+}
+
+template <typename F>
+inline cudaError_t set_smem(F fn, size_t smem) {
+    if (smem > 48 * 1024)
+        return cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaSuccess;
+}
+
+constexpr int kBlock = 256;
+
+inline int grid_of(uint64_t work_items, uint64_t per_block, int sm_count, int occ) {
+    const uint64_t need = (work_items + per_block - 1) / per_block;
+    return (int)std::min<uint64_t>(need, (uint64_t)sm_count * std::max(occ, 1));
+}
+
+template <typename T, typename I, int MD, bool EX>
 cudaError_t launch_dense(const GatePlan &g, void *psi, int sm_count, cudaStream_t s) {
-    constexpr int kBlock = 256;
     if (g.mode == Mode::Direct) {
-        DenseDirectArgs<T, MD> a;
+        DenseDirectArgs<T, I, MD> a;
         a.psi = static_cast<v2<T> *>(psi);
-        a.R = g.R;
-        a.base = g.base_off;
+        a.R = (I)g.R;
+        a.base = (I)g.base_off;
         a.D = g.D;
-        a.ex = g.ex;
-        for (int j = 0; j < MD; ++j) a.off[j] = j < g.D ? g.off[j] : 0;
-        for (int i = 0; i < MD; ++i)
-            for (int j = 0; j < MD; ++j)
-                a.U[i * MD + j] = (i < g.D && j < g.D) ? mk<T>((T)g.U[2 * (i * g.D + j)], (T)g.U[2 * (i * g.D + j) + 1])
-                                                       : mk<T>(T(0), T(0));
-        auto fn = k_dense_direct<T, MD, EX>;
-        const int occ = occupancy_blocks((const void *)fn, kBlock, 0);
-        const uint64_t need = (g.R + kBlock - 1) / kBlock;
-        const int grid = (int)std::min<uint64_t>(need, (uint64_t)sm_count * occ);
+        a.ex = expand_for<I>(g.ex);
+        for (int j = 0; j < MD; ++j) a.off[j] = j < g.D ? (I)g.off[j] : 0;
+        fill_matrix<T, MD>(a.U, a.Ulo, g);
+        auto fn = k_dense_direct<T, I, MD, EX>;
+        const int grid = grid_of(g.R, kBlock, sm_count, occupancy_blocks((const void *)fn, kBlock, 0));
         if (grid <= 0) return cudaSuccess;
         fn<<<grid, kBlock, 0, s>>>(a);
         return cudaGetLastError();
     }
-    DenseTileArgs<T, MD> a;
+    DenseTileArgs<T, I, MD> a;
     a.psi = static_cast<v2<T> *>(psi);
     a.D = g.D;
-    fill_tilegeo<T>(a.t, g);
+    fill_tilegeo<I>(a.t, g);
     for (int j = 0; j < MD; ++j) {
-        a.offH[j] = j < (int)g.DH ? g.offH[j] : 0;
+        a.offH[j] = j < (int)g.DH ? (I)g.offH[j] : 0;
         a.smoff[j] = j < g.D ? g.smoff[j] : 0;
     }
-    for (int i = 0; i < MD; ++i)
-        for (int j = 0; j < MD; ++j)
-            a.U[i * MD + j] = (i < g.D && j < g.D) ? mk<T>((T)g.U[2 * (i * g.D + j)], (T)g.U[2 * (i * g.D + j) + 1])
-                                                   : mk<T>(T(0), T(0));
-    auto fn = k_dense_tile<T, MD, EX>;
-    const size_t smem = tile_smem_bytes(g, sizeof(v2<T>));
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    const int occ = occupancy_blocks((const void *)fn, kBlock, smem);
-    const uint64_t need = (g.R_tiles + g.tpc - 1) / g.tpc;
-    const int grid = (int)std::min<uint64_t>(need, (uint64_t)sm_count * std::max(occ, 1));
+    fill_matrix<T, MD>(a.U, a.Ulo, g);
+    auto fn = k_dense_tile<T, I, MD, EX>;
+    const size_t smem = tile_smem_bytes<I>(g, sizeof(v2<T>));
+    cudaError_t e = set_smem(fn, smem);
+    if (e != cudaSuccess) return e;
+    const int grid = grid_of(g.R_tiles, g.tpc, sm_count, occupancy_blocks((const void *)fn, kBlock, smem));
     if (grid <= 0) return cudaSuccess;
     fn<<<grid, kBlock, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-template <typename T, int MD>
+template <typename T, typename I, int MD>
 cudaError_t launch_mono(const GatePlan &g, void *psi, int sm_count, cudaStream_t s) {
-    constexpr int kBlock = 256;
     if (g.mode == Mode::Direct) {
-        MonoDirectArgs<T, MD> a;
+        MonoDirectArgs<T, I, MD> a;
         a.psi = static_cast<v2<T> *>(psi);
-        a.R = g.R;
-        a.base = g.base_off;
+        a.R = (I)g.R;
+        a.base = (I)g.base_off;
         a.active = g.active;
         a.unit = g.unit;
-        a.ex = g.ex;
+        a.ex = expand_for<I>(g.ex);
         for (int i = 0; i < MD; ++i) {
             const bool in = i < g.D;
-            a.off[i] = in ? g.off[i] : 0;
-            a.offsrc[i] = in ? g.off[g.src[i]] : 0;
-            a.lam[i] = in ? mk<T>((T)g.lam[2 * i], (T)g.lam[2 * i + 1]) : mk<T>(T(1), T(0));
+            a.off[i] = in ? (I)g.off[i] : 0;
+            a.offsrc[i] = in ? (I)g.off[g.src[i]] : 0;
         }
-        auto fn = k_mono_direct<T, MD>;
-        const int occ = occupancy_blocks((const void *)fn, kBlock, 0);
-        const uint64_t need = (g.R + kBlock - 1) / kBlock;
-        const int grid = (int)std::min<uint64_t>(need, (uint64_t)sm_count * occ);
+        fill_lam<T, MD>(a.lam, a.lamlo, g);
+        auto fn = k_mono_direct<T, I, MD>;
+        const int grid = grid_of(g.R, kBlock, sm_count, occupancy_blocks((const void *)fn, kBlock, 0));
         if (grid <= 0) return cudaSuccess;
         fn<<<grid, kBlock, 0, s>>>(a);
         return cudaGetLastError();
     }
-    MonoTileArgs<T, MD> a;
+    MonoTileArgs<T, I, MD> a;
     a.psi = static_cast<v2<T> *>(psi);
     a.active = g.active;
     a.unit = g.unit;
-    fill_tilegeo<T>(a.t, g);
+    fill_tilegeo<I>(a.t, g);
     for (int i = 0; i < MD; ++i) {
         const bool in = i < g.D;
-        a.offH[i] = i < (int)g.DH ? g.offH[i] : 0;
+        a.offH[i] = i < (int)g.DH ? (I)g.offH[i] : 0;
         a.smoff[i] = in ? g.smoff[i] : 0;
         a.smoffsrc[i] = in ? g.smoff[g.src[i]] : 0;
-        a.lam[i] = in ? mk<T>((T)g.lam[2 * i], (T)g.lam[2 * i + 1]) : mk<T>(T(1), T(0));
     }
-    auto fn = k_mono_tile<T, MD>;
-    const size_t smem = tile_smem_bytes(g, sizeof(v2<T>));
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    const int occ = occupancy_blocks((const void *)fn, kBlock, smem);
-    const uint64_t need = (g.R_tiles + g.tpc - 1) / g.tpc;
-    const int grid = (int)std::min<uint64_t>(need, (uint64_t)sm_count * std::max(occ, 1));
+    fill_lam<T, MD>(a.lam, a.lamlo, g);
+    auto fn = k_mono_tile<T, I, MD>;
+    const size_t smem = tile_smem_bytes<I>(g, sizeof(v2<T>));
+    cudaError_t e = set_smem(fn, smem);
+    if (e != cudaSuccess) return e;
+    const int grid = grid_of(g.R_tiles, g.tpc, sm_count, occupancy_blocks((const void *)fn, kBlock, smem));
     if (grid <= 0) return cudaSuccess;
     fn<<<grid, kBlock, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+template <typename T, typename I>
+cudaError_t launch_gate_ti(const GatePlan &g, void *psi, int sm_count, cudaStream_t s) {
+    if (g.kind == Kind::Mono) {
+        if (g.D <= 4) return launch_mono<T, I, 4>(g, psi, sm_count, s);
+        if (g.D <= 8) return launch_mono<T, I, 8>(g, psi, sm_count, s);
+        if (g.D <= 16) return launch_mono<T, I, 16>(g, psi, sm_count, s);
+        return launch_mono<T, I, 32>(g, psi, sm_count, s);
+    }
+    switch (g.D) {
+        case 2: return launch_dense<T, I, 2, true>(g, psi, sm_count, s);
+        case 3: return launch_dense<T, I, 3, true>(g, psi, sm_count, s);
+        case 4: return launch_dense<T, I, 4, true>(g, psi, sm_count, s);
+        case 5: return launch_dense<T, I, 5, true>(g, psi, sm_count, s);
+        case 6: return launch_dense<T, I, 6, true>(g, psi, sm_count, s);
+        case 8: return launch_dense<T, I, 8, true>(g, psi, sm_count, s);
+        case 9: return launch_dense<T, I, 9, true>(g, psi, sm_count, s);
+        default: break;
+    }
+    if (g.D <= 16) return launch_dense<T, I, 16, false>(g, psi, sm_count, s);
+    return launch_dense<T, I, 32, false>(g, psi, sm_count, s);
 }
 
 template <typename T>
 cudaError_t launch_gate_t(const GatePlan &g, void *psi, int sm_count, cudaStream_t s) {
-    if (g.kind == Kind::Mono) {
-        if (g.D <= 4) return launch_mono<T, 4>(g, psi, sm_count, s);
-        if (g.D <= 8) return launch_mono<T, 8>(g, psi, sm_count, s);
-        if (g.D <= 16) return launch_mono<T, 16>(g, psi, sm_count, s);
-        return launch_mono<T, 32>(g, psi, sm_count, s);
-    }
-    switch (g.D) {
-        case 2: return launch_dense<T, 2, true>(g, psi, sm_count, s);
-        case 3: return launch_dense<T, 3, true>(g, psi, sm_count, s);
-        case 4: return launch_dense<T, 4, true>(g, psi, sm_count, s);
-        case 5: return launch_dense<T, 5, true>(g, psi, sm_count, s);
-        case 6: return launch_dense<T, 6, true>(g, psi, sm_count, s);
-        case 8: return launch_dense<T, 8, true>(g, psi, sm_count, s);
-        case 9: return launch_dense<T, 9, true>(g, psi, sm_count, s);
-        default: break;
-    }
-    if (g.D <= 16) return launch_dense<T, 16, false>(g, psi, sm_count, s);
-    return launch_dense<T, 32, false>(g, psi, sm_count, s);
+    if (g.N < (uint64_t(1) << 31)) return launch_gate_ti<T, uint32_t>(g, psi, sm_count, s);
+    return launch_gate_ti<T, uint64_t>(g, psi, sm_count, s);
 }
 
 }  // namespace qd

@@ -135,4 +135,20 @@ __host__ __device__ __forceinline__ uint32_t expand(uint32_t r, const Expand32 &
     return r;
 }
 
+// Index width of a launch: 32-bit arithmetic when every index of the register
+// is below 2^31 (FastDiv32's dividend bound), 64-bit otherwise.
+template <typename I> struct ExpandOf;
+template <> struct ExpandOf<uint32_t> { using type = Expand32; };
+template <> struct ExpandOf<uint64_t> { using type = Expand64; };
+
+inline Expand32 narrow(const Expand64 &e) {
+    Expand32 r{};
+    r.n = e.n;
+    for (int k = 0; k < e.n; ++k) {
+        r.div[k] = make_fastdiv32((uint32_t)e.div[k].d);
+        r.span[k] = (uint32_t)e.span[k];
+    }
+    return r;
+}
+
 }  // namespace qd

@@ -16,14 +16,18 @@ enum class Kind : int32_t { Dense = 0, Mono = 1 };
 // a coalescing width.
 constexpr uint32_t kTileBudget = 2048;
 constexpr uint32_t kTileHardMax = 8192;
-// A target or control qudit with flat stride below this many amplitudes makes
-// the direct kernel's warps read short strided runs; such gates use tile mode.
-constexpr int64_t kLowStride = 32;
+// Default stride threshold of tile mode: a gate whose lowest target or control
+// stride is below it is staged through shared memory.  Measured on GB300 the
+// direct kernel is faster for every stride (L1 absorbs the short strided
+// runs), so the default is 0 (never tile); QD_TILE_STRIDE in the environment
+// or qd_set_tuning(QD_TUNE_TILE_STRIDE) per register override it.
+constexpr int64_t kLowStride = 0;
 
 struct GatePlan {
     Mode mode = Mode::Direct;
     Kind kind = Kind::Dense;
     int32_t D = 0;
+    uint64_t N = 0;  // register size (selects 32- or 64-bit index arithmetic)
 
     // --- direct mode: one thread per group --------------------------------
     uint64_t R = 0;          // number of groups

@@ -22,6 +22,7 @@ QD_HOST, QD_DEVICE = 0, 1
 QD_GATE_X, QD_GATE_Z, QD_GATE_H, QD_GATE_U, QD_GATE_DIAG = 1, 2, 3, 4, 5
 QD_PLAN_NONE, QD_PLAN_GREEDY, QD_PLAN_LEARNED, QD_PLAN_EXHAUSTIVE = 0, 1, 2, 3
 QD_MAX_TARGETS, QD_MAX_CONTROLS = 6, 8
+QD_TUNE_TILE_STRIDE = 1
 ERRORS = {-1: "QD_ERR_ARG", -2: "QD_ERR_DIM", -3: "QD_ERR_OVERLAP", -4: "QD_ERR_OOM", -5: "QD_ERR_CUDA",
           -6: "QD_ERR_TIMEOUT", -7: "QD_ERR_DEVICE", -8: "QD_ERR_UNSUPPORTED"}
 
@@ -54,6 +55,7 @@ _SIGS = {
     "qd_reset": [_vp, _i32p],
     "qd_info": [_vp, _i64p, _i32p, ctypes.POINTER(_vp), _i32p],
     "qd_set_stream": [_vp, _vp],
+    "qd_set_tuning": [_vp, _i32, _i64],
     "qd_apply": [_vp, _dp, _i32p, _i32, _i32p, _i32p, _i32],
     "qd_apply_diag": [_vp, _dp, _i32p, _i32, _i32p, _i32p, _i32],
     "qd_apply_x": [_vp, _i32, _i32],
@@ -150,6 +152,10 @@ def qd_info(reg: int) -> dict:
 
 def qd_set_stream(reg: int, stream: int) -> None:
     _check(load().qd_set_stream(_vp(reg), _vp(stream or None)))
+
+
+def qd_set_tuning(reg: int, key: int, value: int) -> None:
+    _check(load().qd_set_tuning(_vp(reg), key, value))
 
 
 # ---- gates ------------------------------------------------------------------
@@ -369,10 +375,13 @@ def qd_last_error() -> str:
 class Register:
     """Owns one qd_reg handle (convenience wrapper, marshalling only)."""
 
-    def __init__(self, dims, init_levels=None, precision=QD_C64, dev_buf=0, dev_buf_bytes=0, stream=0):
+    def __init__(self, dims, init_levels=None, precision=QD_C64, dev_buf=0, dev_buf_bytes=0, stream=0,
+                 tile_stride=None):
         self.dims = [int(d) for d in dims]
         self.precision = precision
         self.h = qd_create(self.dims, init_levels, precision, dev_buf, dev_buf_bytes, stream)
+        if tile_stride is not None:
+            qd_set_tuning(self.h, QD_TUNE_TILE_STRIDE, tile_stride)
 
     def close(self):
         if self.h:
@@ -400,19 +409,19 @@ class Register:
 
 # ---- host-only planner inspection (include/qudit_debug.h) ------------------
 
-def qd_debug_gate_members(dims: Sequence[int], gate, cap: int = 1 << 20):
+def qd_debug_gate_members(dims: Sequence[int], gate, cap: int = 1 << 20, tile_stride: int = -1):
     """Replay the planned kernel's index arithmetic on the host.
 
     Returns (members[groups, D] int64, info dict); see include/qudit_debug.h."""
     L = load()
-    fn = L.qd_debug_gate_members
-    fn.argtypes = [_i32p, _i32, ctypes.POINTER(QdGate), _i64p, _i64, _i64p]
+    fn = L.qd_debug_gate_members_tuned
+    fn.argtypes = [_i32p, _i32, ctypes.POINTER(QdGate), _i64, _i64p, _i64, _i64p]
     fn.restype = ctypes.c_int
     d, dp = _arr_i32(dims)
     ga = GateArray([gate])
     out = np.zeros(cap, dtype=np.int64)
     info = np.zeros(7, dtype=np.int64)
-    _check(fn(dp, len(d), ga.ptr, out.ctypes.data_as(_i64p), cap, info.ctypes.data_as(_i64p)))
+    _check(fn(dp, len(d), ga.ptr, tile_stride, out.ctypes.data_as(_i64p), cap, info.ctypes.data_as(_i64p)))
     keys = ["mode", "D", "groups", "kind", "active", "B", "noop"]
     inf = {k: int(v) for k, v in zip(keys, info)}
     if inf["noop"]:
@@ -420,3 +429,7 @@ def qd_debug_gate_members(dims: Sequence[int], gate, cap: int = 1 << 20):
     n = inf["groups"] * inf["D"]
     assert n <= cap
     return out[:n].reshape(inf["groups"], inf["D"]), inf
+
+
+def qd_debug_gate_members_tuned(dims: Sequence[int], gate, tile_stride: int, cap: int = 1 << 20):
+    return qd_debug_gate_members(dims, gate, cap, tile_stride)

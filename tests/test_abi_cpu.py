@@ -79,8 +79,8 @@ def _oracle_groups(dims, gate):
     return {tuple(int(b + o) for o in offs) for b in bases}
 
 
-def _check_gate(dims, gate, expect_mode=None):
-    mem, info = L.qd_debug_gate_members(dims, gate)
+def _check_gate(dims, gate, expect_mode=None, tile_stride=32):
+    mem, info = L.qd_debug_gate_members(dims, gate, tile_stride=tile_stride)
     assert info["noop"] == 0
     got = {tuple(int(x) for x in row) for row in mem}
     assert len(got) == mem.shape[0]            # no group emitted twice
@@ -90,8 +90,9 @@ def _check_gate(dims, gate, expect_mode=None):
     return info
 
 
+@pytest.mark.parametrize("tile_stride", [0, 32, 1000])
 @pytest.mark.parametrize("seed", range(40))
-def test_planner_groups_match_oracle(seed):
+def test_planner_groups_match_oracle(seed, tile_stride):
     rng = np.random.default_rng(seed)
     n = int(rng.integers(2, 8))
     dims = [int(x) for x in rng.choice([2, 3, 4, 5, 7], size=n)]
@@ -107,7 +108,7 @@ def test_planner_groups_match_oracle(seed):
         D = dims[targets[0]]
     levels = tuple(int(rng.integers(0, dims[c])) for c in controls)
     g = Gate("U", tuple(targets), tuple(controls), levels, matrix=wl.haar_unitary(D, rng))
-    _check_gate(dims, g)
+    _check_gate(dims, g, tile_stride=tile_stride)
 
 
 def test_direct_and_tile_modes_are_both_exercised():
@@ -117,6 +118,7 @@ def test_direct_and_tile_modes_are_both_exercised():
     u = wl.haar_unitary(3, rng)
     assert _check_gate(dims, Gate("U", (8,), matrix=u), expect_mode=0)["mode"] == 0
     assert _check_gate(dims, Gate("U", (0,), matrix=u), expect_mode=1)["mode"] == 1
+    assert _check_gate(dims, Gate("U", (0,), matrix=u), expect_mode=0, tile_stride=0)["mode"] == 0
     # low control with high target also takes the tile path
     _check_gate(dims, Gate("X", (7,), (0,), (1,), 2), expect_mode=1)
     # a two-qudit gate spanning low and high qudits

@@ -31,8 +31,8 @@ def _built():
     L.load()
 
 
-def run_gpu(dims, gates, prec, init=None, psi0=None, plan=L.QD_PLAN_NONE):
-    with L.Register(dims, init, prec) as r:
+def run_gpu(dims, gates, prec, init=None, psi0=None, plan=L.QD_PLAN_NONE, tile_stride=None):
+    with L.Register(dims, init, prec, tile_stride=tile_stride) as r:
         if psi0 is not None:
             L.qd_set_amplitudes(r.h, psi0)
         r.run(gates, plan)
@@ -149,14 +149,15 @@ def _random_case(rng, nmax=8, Nmax=60000):
     return dims, gates
 
 
+@pytest.mark.parametrize("tile_stride", [0, 32, 100000])
 @pytest.mark.parametrize("seed", range(24))
 @pytest.mark.parametrize("prec", [L.QD_C128, L.QD_C64])
-def test_random_geometry_sweep(seed, prec):
+def test_random_geometry_sweep(seed, prec, tile_stride):
     rng = np.random.default_rng(500 + seed)
     dims, gates = _random_case(rng)
     psi0 = rand_state(rng, qo.register_size(dims))
     ref = qf.run_circuit(dims, gates, psi0=psi0)
-    psi = run_gpu(dims, gates, prec, psi0=psi0)
+    psi = run_gpu(dims, gates, prec, psi0=psi0, tile_stride=tile_stride)
     check(psi, ref, prec)
 
 
@@ -180,8 +181,9 @@ def test_controlled_leaves_other_levels_bit_identical(prec):
         check(after.astype(np.complex128), qo.loop_apply(before.astype(np.complex128), dims, g), prec)
 
 
+@pytest.mark.parametrize("tile_stride", [0, 32])
 @pytest.mark.parametrize("prec", [L.QD_C128, L.QD_C64])
-def test_large_dims_and_three_targets(prec):
+def test_large_dims_and_three_targets(prec, tile_stride):
     rng = np.random.default_rng(21)
     dims = [31, 2, 17, 3]
     N = qo.register_size(dims)
@@ -192,7 +194,7 @@ def test_large_dims_and_three_targets(prec):
              Gate("H", (3,), (0, 2), (3, 16)),
              Gate("U", (3, 1), (2,), (5,), matrix=wl.haar_unitary(6, rng))]
     ref = qf.run_circuit(dims, gates, psi0=psi0)
-    check(run_gpu(dims, gates, prec, psi0=psi0), ref, prec)
+    check(run_gpu(dims, gates, prec, psi0=psi0, tile_stride=tile_stride), ref, prec)
 
 
 def test_single_qudit_register_and_d64():
@@ -222,11 +224,17 @@ def test_identity_gate_is_noop():
 
 # ----------------------------------------------------------------- C1 config
 
-@pytest.mark.parametrize("prec", [L.QD_C128, L.QD_C64])
-def test_c1_full_size(prec):
+@pytest.fixture(scope="module")
+def c1_reference():
     dims, gates = wl.circuit_c1()
-    ref = qf.run_circuit(dims, gates)
-    psi = run_gpu(dims, gates, prec)
+    return dims, gates, qf.run_circuit(dims, gates)
+
+
+@pytest.mark.parametrize("tile_stride", [0, 32])
+@pytest.mark.parametrize("prec", [L.QD_C128, L.QD_C64])
+def test_c1_full_size(prec, tile_stride, c1_reference):
+    dims, gates, ref = c1_reference
+    psi = run_gpu(dims, gates, prec, tile_stride=tile_stride)
     check(psi, ref, prec)
 
 
