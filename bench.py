@@ -116,10 +116,14 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+KERNEL_SOURCES = ("qd_apply.cuh", "qd_common.cuh", "qd_plan.h")
+
+
 def kernel_source_sha():
+    """Hash of the per-gate kernel sources (the dominant kernel's code)."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2211_07918_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in KERNEL_SOURCES:
         with open(os.path.join(d, f), "rb") as fh:
             h.update(f.encode())
             h.update(fh.read())

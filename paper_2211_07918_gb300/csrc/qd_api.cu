@@ -319,7 +319,8 @@ int plan_gate(const qd_reg *r, const double *M, const Acting &a, bool diag_only,
         return v ? (int64_t)std::atoll(v) : kLowStride;
     }();
     const int64_t low_stride = r->tile_stride >= 0 ? r->tile_stride : default_low_stride;
-    if (min_stride >= low_stride) {
+    // direct geometry (always computed: it is the fallback of tile mode)
+    {
         g.mode = Mode::Direct;
         g.R = (uint64_t)(r->N / (D * cprod));
         std::vector<std::pair<int64_t, int64_t>> ins;
@@ -331,11 +332,10 @@ int plan_gate(const qd_reg *r, const double *M, const Acting &a, bool diag_only,
             }
         set_expand64(g.ex, ins);
         g.base_off = base;
-        return QD_OK;
     }
+    if (min_stride >= low_stride) return QD_OK;
 
-    // ---- tile mode ----
-    g.mode = Mode::Tile;
+    // ---- tile mode (falls back to direct when the tile would not fit) ----
     int m = 0;
     for (int q = 0; q < n; ++q)
         if ((is_t[q] || is_c[q]) && s[q] < low_stride) m = q + 1;
@@ -365,7 +365,8 @@ int plan_gate(const qd_reg *r, const double *M, const Acting &a, bool diag_only,
         }
         break;
     }
-    if (B * DH > (int64_t)kTileHardMax) return fail(QD_ERR_UNSUPPORTED, "gate geometry exceeds the tile limit");
+    if (B * DH > (int64_t)kTileHardMax) return QD_OK;  // stays in direct mode
+    g.mode = Mode::Tile;
     g.B = (uint32_t)B;
     g.DH = (uint32_t)DH;
     // high (>= m) removed digits: expansion over block-level strides s_q / B
