@@ -208,6 +208,26 @@ int qd_sample(qd_reg *reg, uint64_t seed, int64_t shots, int64_t *out);
 /* The same with caller-supplied uniforms u[0..shots) in [0,1) (host). */
 int qd_sample_u(qd_reg *reg, const double *u, int64_t shots, int64_t *out);
 
+/* Prefix sums without any device allocation.  The paper has no counterpart
+ * to this call; it exists for callers that may not allocate device memory,
+ * such as code running under an application allocator that owns all of the
+ * device heap, or a latency-critical loop where an allocation (which can
+ * synchronise the device) is not allowed.
+ * It writes the same inclusive FP64 prefix sums of |state_i|^2 as qd_cdf to
+ * the caller's device buffer cdf_out[0..n_amplitudes), reading the caller's
+ * device state (QD_C64 or QD_C128 amplitudes), on stream (cudaStream_t as
+ * void*, NULL = legacy default stream); it returns once the work is enqueued.
+ * Its scratch is a fixed array of 65536 FP64 chunk sums inside the library's
+ * device image (512 KiB, held on every GPU that loads the library until the
+ * process exits), so n_amplitudes may not exceed 2^28 (QD_ERR_DIM beyond).
+ * The first call on each device looks up the array's device address with
+ * that device current; make that first call before any stream capture.
+ * All calls share the one array: calls whose work overlaps on the GPU (for
+ * example on two streams at once) race on it and must be ordered by the
+ * caller.  Values an earlier call left in the array are never read.
+ * Errors: QD_ERR_ARG (null pointer, bad precision), QD_ERR_DIM, QD_ERR_CUDA. */
+int qd_cdf_noalloc(const void *state, int64_t n_amplitudes, int32_t precision, double *cdf_out, void *stream);
+
 /* Copy the N amplitudes out of / into the register (register precision). */
 int qd_get_amplitudes(qd_reg *reg, void *out, int32_t where);
 int qd_set_amplitudes(qd_reg *reg, const void *in, int32_t where);

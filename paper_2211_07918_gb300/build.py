@@ -25,6 +25,7 @@ SOURCES = [
     "qd_apply_f32.cu",
     "qd_apply_f64.cu",
     "qd_reduce.cu",
+    "qd_noalloc.cu",
 ]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

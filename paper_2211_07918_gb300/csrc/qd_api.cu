@@ -90,6 +90,8 @@ struct qd_plan {
 };
 
 namespace qd {
+int set_last_error(int code, const char *msg) { return fail(code, msg); }
+
 int occupancy_blocks(const void *fn, int block, size_t smem) {
     static std::mutex mu;
     static std::map<std::pair<const void *, size_t>, int> cache;

@@ -80,6 +80,7 @@ _SIGS = {
     "qd_get_amplitudes": [_vp, _vp, _i32],
     "qd_set_amplitudes": [_vp, _vp, _i32],
     "qd_sync": [_vp, _i32p],
+    "qd_cdf_noalloc": [_vp, _i64, _i32, _dp, _vp],
 }
 
 
@@ -334,6 +335,12 @@ def qd_sample_u(reg: int, u) -> np.ndarray:
     out = np.empty(len(u), dtype=np.int64)
     _check(load().qd_sample_u(_vp(reg), u.ctypes.data_as(_dp), len(u), out.ctypes.data_as(_i64p)))
     return out
+
+
+def qd_cdf_noalloc(state_ptr: int, n_amplitudes: int, precision: int, cdf_out_ptr: int, stream: int = 0) -> None:
+    """Prefix sums into a caller-provided device buffer; allocates nothing."""
+    _check(load().qd_cdf_noalloc(_vp(state_ptr), n_amplitudes, precision, ctypes.cast(_vp(cdf_out_ptr), _dp),
+                                 _vp(stream or None)))
 
 
 def qd_get_amplitudes(reg: int, out: Optional[np.ndarray] = None) -> np.ndarray:
