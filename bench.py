@@ -240,11 +240,11 @@ def run_ours(args, rank, world, local):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     probs = torch.empty(N, dtype=torch.float64, device=dev)
 
-    def measure(prec, steps, warmup, profile_steps):
+    def measure(prec, steps, warmup, profile_steps, plan_kind=L.QD_PLAN_NONE):
         """K timed steps with the plan replayed as a CUDA graph (the headline),
         then ``profile_steps`` steps with per-launch events (kernel times)."""
         reg = L.qd_create(dims, None, prec, 0, 0, stream.cuda_stream)
-        plan = L.qd_plan_create(reg, gates, L.QD_PLAN_NONE)
+        plan = L.qd_plan_create(reg, gates, plan_kind)
         launches = L.qd_plan_info(plan)["launches"]
 
         def step():
@@ -292,6 +292,11 @@ def run_ours(args, rank, world, local):
     wall = time.perf_counter() - t_wall
     clocks = sampler.stop()
     ms128, _, _ = measure(L.QD_C128, max(3, args.steps // 4), args.warmup, 0)
+    fused = {}
+    for name, kind in (("greedy", L.QD_PLAN_GREEDY), ("exhaustive", L.QD_PLAN_EXHAUSTIVE)):
+        msf, _, nlaunch = measure(L.QD_C64, max(3, args.steps // 2), args.warmup, 0, kind)
+        fused[name] = {"gates_per_s": world * ngates / (float(np.mean(msf)) * 1e-3),
+                       "ms_per_step": float(np.mean(msf)), "launches": nlaunch}
     prof_steps = kern64.pop("_steps")
 
     total_ms = float(sum(ms64))
@@ -380,7 +385,9 @@ def run_ours(args, rank, world, local):
             "compare": {"complex128_gates_per_s": world * ngates / (ms_step128 * 1e-3),
                         "complex128_ms_per_step": ms_step128,
                         "c64_over_c128": ms_step128 / ms_step,
-                        "c64_fidelity_vs_c128": fid, "c64_maxabs_vs_c128": maxabs},
+                        "c64_fidelity_vs_c128": fid, "c64_maxabs_vs_c128": maxabs,
+                        "fused_complex64": fused,
+                        "fused_greedy_over_c128": fused["greedy"]["gates_per_s"] / (world * ngates / (ms_step128 * 1e-3))},
             "roofline": roofline,
             "clocks": clocks,
             "e2e": e2e,

@@ -128,6 +128,11 @@ int qd_set_stream(qd_reg *reg, void *stream);
  * kernels); 0 never tiles.  Default: environment QD_TILE_STRIDE, else 0.
  * Errors: QD_ERR_ARG for an unknown key or a negative value. */
 #define QD_TUNE_TILE_STRIDE 1
+/* QD_TUNE_FUSE_KMAX: most qudits a fused block may span (1..6, default 3).
+ * QD_TUNE_FUSE_DMAX: largest dimension of a fused block (2..QD_MAX_D,
+ * default 32). */
+#define QD_TUNE_FUSE_KMAX 2
+#define QD_TUNE_FUSE_DMAX 3
 int qd_set_tuning(qd_reg *reg, int32_t key, int64_t value);
 
 /* ---- gate application, in place (Sec. 2.1.2, Sec. 3.4) ---------------- */
@@ -164,7 +169,15 @@ int qd_apply_gate(qd_reg *reg, const qd_gate *gate);
 
 /* Validate and prepare a gate list for repeated runs on this register:
  * kernel choice, launch parameters and (plan_kind != QD_PLAN_NONE) gate
- * fusion.  The gates array and its matrices may be freed after the call. */
+ * fusion.  Fusion splits the gate list into contiguous segments; a segment of
+ * several gates becomes one dense block (the FP64 product of its gates,
+ * controls expanded, over the union of their qudits, at most
+ * QD_TUNE_FUSE_KMAX qudits and QD_TUNE_FUSE_DMAX states) applied in one pass.
+ * QD_PLAN_GREEDY extends a segment while the cost model prefers the merged
+ * block; QD_PLAN_EXHAUSTIVE takes the exact minimum-cost segmentation.
+ * Identity gates are dropped.  The gates array and its matrices may be freed
+ * after the call.  Errors: those of the gates (prefixed with the gate index),
+ * QD_ERR_UNSUPPORTED for a plan kind without its cost model. */
 int qd_plan_create(qd_reg *reg, const qd_gate *gates, int32_t ngates, int32_t plan_kind, qd_plan **out);
 /* Enqueue the prepared circuit on the register's stream.  On a non-default
  * stream the first run captures the launches into a CUDA graph and later runs

@@ -27,6 +27,25 @@ int qd_debug_gate_members(const int32_t *dims, int32_t n, const qd_gate *gate, i
 /* The same with an explicit tile-stride threshold (see QD_TUNE_TILE_STRIDE). */
 int qd_debug_gate_members_tuned(const int32_t *dims, int32_t n, const qd_gate *gate, int64_t tile_stride,
                                 int64_t *out, int64_t cap, int64_t *info);
+
+/* Fusion planner replay (host only, no device).  For a register of dims[0..n)
+ * at `precision`, plan gates[0..ngates) with plan_kind and the fusion limits
+ * kmax, dmax (as QD_TUNE_FUSE_KMAX / QD_TUNE_FUSE_DMAX): writes the chosen
+ * contiguous segments as [seg_first[i], seg_last[i]] gate ranges (indices of
+ * the non-identity gates, in order; up to cap), their count in *nseg, and the
+ * cost model's total in *model_cost. */
+int qd_debug_fuse_plan(const int32_t *dims, int32_t n, int32_t precision, const qd_gate *gates, int32_t ngates,
+                       int32_t plan_kind, int32_t kmax, int32_t dmax, int32_t *seg_first, int32_t *seg_last,
+                       int32_t cap, int32_t *nseg, double *model_cost);
+/* Cost the model assigns to the segment [first, last] of the non-identity
+ * gates (one gate: its own kernel; several: one dense block). */
+int qd_debug_segment_cost(const int32_t *dims, int32_t n, int32_t precision, const qd_gate *gates, int32_t ngates,
+                          int32_t first, int32_t last, double *cost);
+/* The fused block of gates [first, last]: its qudits (first = most
+ * significant local digit, at most 6) and its D x D FP64 matrix (interleaved
+ * complex, row-major; cap doubles available). */
+int qd_debug_fuse_block(const int32_t *dims, int32_t n, const qd_gate *gates, int32_t ngates, int32_t first,
+                        int32_t last, int32_t *qudits, int32_t *k, int32_t *D, double *matrix, int64_t cap);
 #ifdef __cplusplus
 }
 #endif

@@ -26,6 +26,7 @@ SOURCES = [
     "qd_apply_f64.cu",
     "qd_reduce.cu",
     "qd_noalloc.cu",
+    "qd_fuse.cu",
 ]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -22,6 +22,7 @@
 
 #include "../../include/qudit.h"
 #include "../../include/qudit_debug.h"
+#include "qd_fuse.h"
 #include "qd_plan.h"
 #include "qd_reduce.h"
 
@@ -68,6 +69,8 @@ struct qd_reg {
     double *cdf_chunks = nullptr;
     int32_t *dev_err = nullptr;
     int64_t tile_stride = -1;  // -1: process default
+    int32_t fuse_kmax = 3;     // largest number of qudits of a fused block
+    int32_t fuse_dmax = 32;    // largest dimension of a fused block
 };
 
 struct qd_plan {
@@ -688,9 +691,22 @@ int qd_set_stream(qd_reg *r, void *stream) {
 
 int qd_set_tuning(qd_reg *r, int32_t key, int64_t value) {
     if (int rc = reg_ok(r)) return rc;
-    if (key != QD_TUNE_TILE_STRIDE || value < 0) return fail(QD_ERR_ARG, "unknown tuning key or negative value");
-    r->tile_stride = value;
-    return QD_OK;
+    switch (key) {
+        case QD_TUNE_TILE_STRIDE:
+            if (value < 0) return fail(QD_ERR_ARG, "tile stride must be >= 0");
+            r->tile_stride = value;
+            return QD_OK;
+        case QD_TUNE_FUSE_KMAX:
+            if (value < 1 || value > QD_MAX_TARGETS) return fail(QD_ERR_ARG, "fusion qudit limit must be in [1, 6]");
+            r->fuse_kmax = (int32_t)value;
+            return QD_OK;
+        case QD_TUNE_FUSE_DMAX:
+            if (value < 2 || value > QD_MAX_D) return fail(QD_ERR_ARG, "fusion dimension limit must be in [2, QD_MAX_D]");
+            r->fuse_dmax = (int32_t)value;
+            return QD_OK;
+        default:
+            return fail(QD_ERR_ARG, "unknown tuning key");
+    }
 }
 
 int qd_apply(qd_reg *r, const double *matrix, const int32_t *targets, int32_t k, const int32_t *controls,
@@ -746,25 +762,131 @@ int qd_apply_gate(qd_reg *r, const qd_gate *gate) {
     return apply_record(r, gate);
 }
 
+}  // extern "C"
+
+namespace {
+
+RegisterShape shape_of(const qd_reg *r) { return RegisterShape{r->n, r->dims, r->s, r->N, r->prec}; }
+
+// Validate every gate, drop identities, and collect both the fusion view
+// (matrix over controls + targets) and the original records.
+int collect_gates(const qd_reg *r, const qd_gate *gates, int32_t ngates, std::vector<FuseGate> &fg,
+                  std::vector<const qd_gate *> &orig) {
+    for (int i = 0; i < ngates; ++i) {
+        const qd_gate *gt = &gates[i];
+        Acting a;
+        int rc = validate(r, gt->targets, gt->k, gt->controls, gt->ctrl_levels, gt->nc, a);
+        if (rc == QD_OK) {
+            std::vector<double> M;
+            bool diag = false;
+            rc = gate_matrix(r, gt, a, M, &diag);
+            GatePlan g;
+            bool noop = false;
+            if (rc == QD_OK) rc = plan_gate(r, M.data(), a, diag, g, &noop);
+            if (rc == QD_OK && !noop) {
+                if (diag) {  // expand the diagonal to a full matrix
+                    std::vector<double> F((size_t)2 * a.D * a.D, 0.0);
+                    for (int j = 0; j < a.D; ++j) {
+                        F[2 * (j * a.D + j)] = M[2 * j];
+                        F[2 * (j * a.D + j) + 1] = M[2 * j + 1];
+                    }
+                    M.swap(F);
+                }
+                std::vector<int> c(a.c, a.c + a.nc), lv(a.lv, a.lv + a.nc), t(a.t, a.t + a.k);
+                fg.push_back(make_fuse_gate(c, lv, t, M, r->dims, g.kind == Kind::Mono));
+                orig.push_back(gt);
+            }
+        }
+        if (rc) {
+            g_last_error = "gate " + std::to_string(i) + ": " + g_last_error;
+            return rc;
+        }
+    }
+    return QD_OK;
+}
+
+CostFn cost_for(const qd_reg *r, int plan_kind) {
+    const RegisterShape sh = shape_of(r);
+    (void)plan_kind;
+    return [sh](const LaunchFeatures &f) { return analytic_cost(sh, f); };
+}
+
+int segments_for(const qd_reg *r, const std::vector<FuseGate> &fg, int plan_kind,
+                 std::vector<std::pair<int, int>> &segs, double *model_cost) {
+    const RegisterShape sh = shape_of(r);
+    const int kmax = r->fuse_kmax, dmax = r->fuse_dmax;
+    CostFn cost = cost_for(r, plan_kind);
+    switch (plan_kind) {
+        case QD_PLAN_NONE:
+            segs.clear();
+            for (int i = 0; i < (int)fg.size(); ++i) segs.push_back({i, i});
+            break;
+        case QD_PLAN_GREEDY:
+            segs = segment_greedy(fg, sh, cost, kmax, dmax);
+            break;
+        case QD_PLAN_EXHAUSTIVE:
+            segs = segment_exhaustive(fg, sh, cost, kmax, dmax, nullptr);
+            break;
+        default:
+            return fail(QD_ERR_UNSUPPORTED, "plan kind not available (learned planning needs a trained cost model)");
+    }
+    if (model_cost) {
+        double c = 0.0;
+        for (auto &sg : segs) c += segment_cost(fg, sg.first, sg.second, sh, cost);
+        *model_cost = c;
+    }
+    return QD_OK;
+}
+
+// Launch plan of one fused block: a dense gate on the block's qudits.
+int plan_block(const qd_reg *r, const FuseBlock &b, GatePlan &g) {
+    Acting a;
+    a.k = (int)b.qudits.size();
+    a.nc = 0;
+    a.D = b.D;
+    if (a.k > QD_MAX_TARGETS || b.D > QD_MAX_D) return fail(QD_ERR_DIM, "fused block too large");
+    for (int m = 0; m < a.k; ++m) a.t[m] = b.qudits[m];
+    bool noop = false;
+    int rc = plan_gate(r, b.M.data(), a, false, g, &noop);
+    if (rc == QD_OK && noop) g = GatePlan{};  // identity block: no launch (D stays 0)
+    return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
 int qd_plan_create(qd_reg *r, const qd_gate *gates, int32_t ngates, int32_t plan_kind, qd_plan **out) {
     if (!out) return fail(QD_ERR_ARG, "null output handle");
     *out = nullptr;
     if (int rc = reg_ok(r)) return rc;
     if (ngates < 0 || (ngates > 0 && !gates)) return fail(QD_ERR_ARG, "bad gate list");
-    if (plan_kind != QD_PLAN_NONE) return fail(QD_ERR_UNSUPPORTED, "fusion plans are not built in this library yet");
+    if (plan_kind < QD_PLAN_NONE || plan_kind > QD_PLAN_EXHAUSTIVE) return fail(QD_ERR_ARG, "unknown plan kind");
+    std::vector<FuseGate> fg;
+    std::vector<const qd_gate *> orig;
+    int rc = collect_gates(r, gates, ngates, fg, orig);
+    if (rc) return rc;
+    std::vector<std::pair<int, int>> segs;
+    if ((rc = segments_for(r, fg, plan_kind, segs, nullptr))) return rc;
     qd_plan *p = new qd_plan();
     p->reg = r;
-    p->gates.reserve(ngates);
-    for (int i = 0; i < ngates; ++i) {
+    p->gates.reserve(segs.size());
+    for (auto &sg : segs) {
         GatePlan g;
-        bool noop = false;
-        int rc = prepare_gate(r, &gates[i], g, &noop);
+        if (sg.first == sg.second) {
+            bool noop = false;
+            rc = prepare_gate(r, orig[sg.first], g, &noop);
+            if (rc == QD_OK && noop) continue;
+        } else {
+            rc = plan_block(r, build_block(fg, sg.first, sg.second, r->dims), g);
+            if (rc == QD_OK && g.D == 0) continue;
+            ++p->blocks;
+        }
         if (rc) {
             delete p;
-            g_last_error = "gate " + std::to_string(i) + ": " + g_last_error;
             return rc;
         }
-        if (!noop) p->gates.push_back(g);
+        p->gates.push_back(g);
     }
     *out = p;
     return QD_OK;
@@ -1072,6 +1194,74 @@ int qd_debug_gate_members_tuned(const int32_t *dims, int32_t n, const qd_gate *g
             }
         }
     }
+    return QD_OK;
+}
+
+namespace {
+int host_register(const int32_t *dims, int32_t n, int32_t precision, qd_reg &r) {
+    if (!dims || n < 1 || n > QD_MAX_QUDITS) return fail(QD_ERR_ARG, "bad dims");
+    r.n = n;
+    int64_t s = 1;
+    for (int q = 0; q < n; ++q) {
+        if (dims[q] < 2 || dims[q] > 64) return fail(QD_ERR_DIM, "qudit dimension must be in [2, 64]");
+        r.dims[q] = dims[q];
+        r.s[q] = s;
+        s *= dims[q];
+    }
+    r.s[n] = s;
+    r.N = s;
+    r.prec = precision == QD_C128 ? QD_C128 : QD_C64;
+    r.esize = r.prec == QD_C64 ? 8 : 16;
+    return QD_OK;
+}
+}  // namespace
+
+int qd_debug_fuse_plan(const int32_t *dims, int32_t n, int32_t precision, const qd_gate *gates, int32_t ngates,
+                       int32_t plan_kind, int32_t kmax, int32_t dmax, int32_t *seg_first, int32_t *seg_last,
+                       int32_t cap, int32_t *nseg, double *model_cost) {
+    qd_reg r;
+    if (int rc = host_register(dims, n, precision, r)) return rc;
+    r.fuse_kmax = kmax;
+    r.fuse_dmax = dmax;
+    std::vector<FuseGate> fg;
+    std::vector<const qd_gate *> orig;
+    if (int rc = collect_gates(&r, gates, ngates, fg, orig)) return rc;
+    std::vector<std::pair<int, int>> segs;
+    if (int rc = segments_for(&r, fg, plan_kind, segs, model_cost)) return rc;
+    for (size_t i = 0; i < segs.size() && (int32_t)i < cap; ++i) {
+        if (seg_first) seg_first[i] = segs[i].first;
+        if (seg_last) seg_last[i] = segs[i].second;
+    }
+    if (nseg) *nseg = (int32_t)segs.size();
+    return QD_OK;
+}
+
+int qd_debug_segment_cost(const int32_t *dims, int32_t n, int32_t precision, const qd_gate *gates, int32_t ngates,
+                          int32_t first, int32_t last, double *cost) {
+    qd_reg r;
+    if (int rc = host_register(dims, n, precision, r)) return rc;
+    std::vector<FuseGate> fg;
+    std::vector<const qd_gate *> orig;
+    if (int rc = collect_gates(&r, gates, ngates, fg, orig)) return rc;
+    if (first < 0 || last < first || last >= (int)fg.size() || !cost) return fail(QD_ERR_ARG, "bad segment");
+    *cost = segment_cost(fg, first, last, shape_of(&r), cost_for(&r, QD_PLAN_GREEDY));
+    return QD_OK;
+}
+
+int qd_debug_fuse_block(const int32_t *dims, int32_t n, const qd_gate *gates, int32_t ngates, int32_t first,
+                        int32_t last, int32_t *qudits, int32_t *k, int32_t *D, double *matrix, int64_t cap) {
+    qd_reg r;
+    if (int rc = host_register(dims, n, QD_C128, r)) return rc;
+    std::vector<FuseGate> fg;
+    std::vector<const qd_gate *> orig;
+    if (int rc = collect_gates(&r, gates, ngates, fg, orig)) return rc;
+    if (first < 0 || last < first || last >= (int)fg.size()) return fail(QD_ERR_ARG, "bad segment");
+    FuseBlock b = build_block(fg, first, last, r.dims);
+    if ((int)b.qudits.size() > 6 || (int64_t)b.M.size() > cap) return fail(QD_ERR_DIM, "block too large for output");
+    for (size_t i = 0; i < b.qudits.size(); ++i) qudits[i] = b.qudits[i];
+    *k = (int32_t)b.qudits.size();
+    *D = b.D;
+    std::copy(b.M.begin(), b.M.end(), matrix);
     return QD_OK;
 }
 

@@ -1,0 +1,79 @@
+// Gate-fusion planner (host): groups runs of consecutive gates into blocks
+// whose product matrix is applied in one pass over the state.
+//
+// A segmentation splits the gate list into contiguous segments; a segment of
+// one gate runs that gate's own kernel, a longer segment runs one dense
+// kernel with the product of its gates embedded in the union of their acting
+// qudits (controls included, expanded to dense).  The greedy planner extends
+// the current segment while the cost model says the merged block is cheaper
+// than closing it; the exhaustive planner is an exact dynamic program over
+// all contiguous segmentations (the judge of the other two).
+#pragma once
+#include <cstdint>
+#include <functional>
+#include <vector>
+
+namespace qd {
+
+// One validated gate: its matrix over the acting qudits (controls first,
+// then targets; first listed = most significant), with controls expanded.
+struct FuseGate {
+    std::vector<int> acting;
+    std::vector<double> M;  // Dact x Dact, interleaved complex, row-major
+    int Dact = 1;
+    bool mono = false;      // the original gate is a permutation with phases
+    int nc = 0;             // number of controls in `acting`
+};
+
+struct FuseBlock {
+    std::vector<int> qudits;  // descending qudit index: first = most significant local digit
+    int D = 1;
+    std::vector<double> M;    // D x D product, interleaved complex
+    int first = 0, last = 0;  // gate range [first, last]
+};
+
+// Features of one candidate launch for the cost models.
+constexpr int kFeatures = 12;
+struct LaunchFeatures {
+    float f[kFeatures];
+};
+
+struct RegisterShape {
+    int n;
+    const int32_t *dims;
+    const int64_t *strides;
+    int64_t N;
+    int precision;  // 1 = complex64, 2 = complex128
+};
+
+// Feature vector of a launch acting on `qudits` with target dimension D:
+// log2 D, qudit count, log2 of the (up to three) smallest strides, relative
+// positions, log2 N, precision, dense flag, log2 of the control-slice
+// fraction.
+LaunchFeatures launch_features(const RegisterShape &reg, const std::vector<int> &qudits, int D, bool dense,
+                               double slice_fraction);
+
+// Analytic cost (seconds): max(HBM time, arithmetic time) + launch overhead,
+// with GB300 rates measured for the per-gate kernels.
+double analytic_cost(const RegisterShape &reg, const LaunchFeatures &f);
+
+using CostFn = std::function<double(const LaunchFeatures &)>;
+
+// Expand a gate over (controls, targets) into its full matrix over `acting`.
+FuseGate make_fuse_gate(const std::vector<int> &controls, const std::vector<int> &levels,
+                        const std::vector<int> &targets, const std::vector<double> &Mt, const int32_t *dims, bool mono);
+
+// Product of gates[first..last] embedded in the union of their qudits.
+FuseBlock build_block(const std::vector<FuseGate> &gates, int first, int last, const int32_t *dims);
+
+// Segmentations: list of [first, last] gate ranges covering the gate list.
+std::vector<std::pair<int, int>> segment_greedy(const std::vector<FuseGate> &gates, const RegisterShape &reg,
+                                                const CostFn &cost, int kmax, int Dmax);
+std::vector<std::pair<int, int>> segment_exhaustive(const std::vector<FuseGate> &gates, const RegisterShape &reg,
+                                                    const CostFn &cost, int kmax, int Dmax, double *best_cost);
+
+// Cost the model assigns to one segment (single gate: its own kernel).
+double segment_cost(const std::vector<FuseGate> &gates, int first, int last, const RegisterShape &reg,
+                    const CostFn &cost);
+
+}  // namespace qd

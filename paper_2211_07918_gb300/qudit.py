@@ -22,7 +22,7 @@ QD_HOST, QD_DEVICE = 0, 1
 QD_GATE_X, QD_GATE_Z, QD_GATE_H, QD_GATE_U, QD_GATE_DIAG = 1, 2, 3, 4, 5
 QD_PLAN_NONE, QD_PLAN_GREEDY, QD_PLAN_LEARNED, QD_PLAN_EXHAUSTIVE = 0, 1, 2, 3
 QD_MAX_TARGETS, QD_MAX_CONTROLS = 6, 8
-QD_TUNE_TILE_STRIDE = 1
+QD_TUNE_TILE_STRIDE, QD_TUNE_FUSE_KMAX, QD_TUNE_FUSE_DMAX = 1, 2, 3
 ERRORS = {-1: "QD_ERR_ARG", -2: "QD_ERR_DIM", -3: "QD_ERR_OVERLAP", -4: "QD_ERR_OOM", -5: "QD_ERR_CUDA",
           -6: "QD_ERR_TIMEOUT", -7: "QD_ERR_DEVICE", -8: "QD_ERR_UNSUPPORTED"}
 
@@ -440,3 +440,52 @@ def qd_debug_gate_members(dims: Sequence[int], gate, cap: int = 1 << 20, tile_st
 
 def qd_debug_gate_members_tuned(dims: Sequence[int], gate, tile_stride: int, cap: int = 1 << 20):
     return qd_debug_gate_members(dims, gate, cap, tile_stride)
+
+
+def qd_debug_fuse_plan(dims, gates, plan_kind, precision=QD_C64, kmax=3, dmax=32):
+    """(segments [(first, last)], model cost) chosen by the host planner."""
+    L = load()
+    fn = L.qd_debug_fuse_plan
+    fn.argtypes = [_i32p, _i32, _i32, ctypes.POINTER(QdGate), _i32, _i32, _i32, _i32, _i32p, _i32p, _i32, _i32p, _dp]
+    fn.restype = ctypes.c_int
+    d, dp = _arr_i32(dims)
+    ga = GateArray(gates)
+    cap = max(1, ga.n)
+    f = np.zeros(cap, np.int32)
+    l = np.zeros(cap, np.int32)
+    ns = _i32()
+    c = ctypes.c_double()
+    _check(fn(dp, len(d), precision, ga.ptr, ga.n, plan_kind, kmax, dmax, f.ctypes.data_as(_i32p),
+              l.ctypes.data_as(_i32p), cap, ctypes.byref(ns), ctypes.byref(c)))
+    return list(zip(f[:ns.value].tolist(), l[:ns.value].tolist())), c.value
+
+
+def qd_debug_segment_cost(dims, gates, first, last, precision=QD_C64):
+    L = load()
+    fn = L.qd_debug_segment_cost
+    fn.argtypes = [_i32p, _i32, _i32, ctypes.POINTER(QdGate), _i32, _i32, _i32, _dp]
+    fn.restype = ctypes.c_int
+    d, dp = _arr_i32(dims)
+    ga = GateArray(gates)
+    c = ctypes.c_double()
+    _check(fn(dp, len(d), precision, ga.ptr, ga.n, first, last, ctypes.byref(c)))
+    return c.value
+
+
+def qd_debug_fuse_block(dims, gates, first, last):
+    """(qudits, D x D complex matrix) of the fused block of gates[first..last]."""
+    L = load()
+    fn = L.qd_debug_fuse_block
+    fn.argtypes = [_i32p, _i32, ctypes.POINTER(QdGate), _i32, _i32, _i32, _i32p, _i32p, _i32p, _dp, _i64]
+    fn.restype = ctypes.c_int
+    d, dp = _arr_i32(dims)
+    ga = GateArray(gates)
+    qs = np.zeros(6, np.int32)
+    k, D = _i32(), _i32()
+    cap = 2 * 1024 * 1024
+    m = np.zeros(cap, np.float64)
+    _check(fn(dp, len(d), ga.ptr, ga.n, first, last, qs.ctypes.data_as(_i32p), ctypes.byref(k), ctypes.byref(D),
+              m.ctypes.data_as(_dp), cap))
+    Dv = D.value
+    M = m[:2 * Dv * Dv].view(np.complex128).reshape(Dv, Dv).copy()
+    return qs[:k.value].tolist(), M

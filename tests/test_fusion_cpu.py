@@ -1,0 +1,115 @@
+"""Fusion planner pins (host only).
+
+* A fused block applied as one matrix over its qudits acts exactly like its
+  gates applied in order (checked with the oracle's index-loop mode).
+* The exhaustive planner's optimum equals brute-force enumeration of every
+  contiguous segmentation under the same cost model (<= 12 gates).
+* Greedy and one-gate-per-launch plans never cost less than the optimum.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+from oracle import qudit_oracle as qo
+from paper_2211_07918_gb300 import qudit as L
+from paper_2211_07918_gb300 import workloads as wl
+from paper_2211_07918_gb300.build import build
+from paper_2211_07918_gb300.workloads import Gate
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build()
+
+
+def _acting(g, dims):
+    return list(g.controls) + list(g.targets)
+
+
+def _circuit(rng, dims, n):
+    mix = ["X", "Z", "H", "CX", "U1", "U2"]
+    gates = []
+    while len(gates) < n:
+        g = wl.random_gate(rng, dims, mix)
+        D = int(np.prod([dims[q] for q in _acting(g, dims)]))
+        if D <= 32:
+            gates.append(g)
+    return gates
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_block_equals_sequential_gates(seed):
+    rng = np.random.default_rng(seed)
+    dims = [int(x) for x in rng.choice([2, 3, 4], size=int(rng.integers(3, 6)))]
+    gates = _circuit(rng, dims, 8)
+    N = qo.register_size(dims)
+    for _ in range(6):
+        a = int(rng.integers(0, len(gates)))
+        b = int(rng.integers(a, min(len(gates), a + 3)))
+        qs, M = L.qd_debug_fuse_block(dims, gates, a, b)
+        psi = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+        want = qo.run_circuit(dims, gates[a:b + 1], psi0=psi)
+        got = qo.loop_apply(psi, dims, Gate("U", tuple(qs), matrix=M))
+        assert np.max(np.abs(got - want)) <= 1e-12
+        assert np.max(np.abs(M @ M.conj().T - np.eye(M.shape[0]))) <= 1e-12
+
+
+def _feasible(gates, dims, a, b, kmax, dmax):
+    if a == b:
+        return True
+    s = set()
+    for g in gates[a:b + 1]:
+        s |= set(_acting(g, dims))
+    return len(s) <= kmax and int(np.prod([dims[q] for q in s])) <= dmax
+
+
+@pytest.mark.parametrize("prec", [L.QD_C64, L.QD_C128])
+@pytest.mark.parametrize("seed", range(8))
+def test_exhaustive_equals_brute_force(seed, prec):
+    rng = np.random.default_rng(40 + seed)
+    dims = [int(x) for x in rng.choice([2, 3, 4], size=5)] + [3] * 9
+    n = int(rng.integers(6, 13))
+    gates = _circuit(rng, dims, n)
+    kmax, dmax = 3, 32
+    cost = {}
+    for a in range(n):
+        for b in range(a, n):
+            if _feasible(gates, dims, a, b, kmax, dmax):
+                cost[(a, b)] = L.qd_debug_segment_cost(dims, gates, a, b, prec)
+    best = np.inf
+    for cuts in itertools.product([0, 1], repeat=n - 1):
+        segs, start = [], 0
+        for i, c in enumerate(cuts):
+            if c:
+                segs.append((start, i))
+                start = i + 1
+        segs.append((start, n - 1))
+        if all(s in cost for s in segs):
+            best = min(best, sum(cost[s] for s in segs))
+    segs, c = L.qd_debug_fuse_plan(dims, gates, L.QD_PLAN_EXHAUSTIVE, prec, kmax, dmax)
+    assert c == pytest.approx(best, rel=1e-12)
+    _, cg = L.qd_debug_fuse_plan(dims, gates, L.QD_PLAN_GREEDY, prec, kmax, dmax)
+    _, cn = L.qd_debug_fuse_plan(dims, gates, L.QD_PLAN_NONE, prec, kmax, dmax)
+    assert cg >= c * (1 - 1e-12) and cn >= c * (1 - 1e-12)
+
+
+@pytest.mark.parametrize("kind", [L.QD_PLAN_NONE, L.QD_PLAN_GREEDY, L.QD_PLAN_EXHAUSTIVE])
+def test_segments_cover_gates_in_order(kind):
+    dims, gates = wl.circuit_c1(ngates=120)
+    segs, _ = L.qd_debug_fuse_plan(dims, gates, kind)
+    nxt = 0
+    for a, b in segs:
+        assert a == nxt and b >= a
+        assert _feasible(gates, dims, a, b, 3, 32)
+        nxt = b + 1
+    assert nxt == len(gates)
+    if kind != L.QD_PLAN_NONE:
+        assert len(segs) < len(gates)
+
+
+def test_identity_gates_are_dropped_before_fusion():
+    dims = [3, 3]
+    gates = [Gate("H", (0,)), Gate("Z", (1,), param=3), Gate("H", (1,))]
+    segs, _ = L.qd_debug_fuse_plan(dims, gates, L.QD_PLAN_NONE)
+    assert len(segs) == 2

@@ -1,0 +1,90 @@
+"""GPU parity of fused plans: the state after a greedy or exhaustive fused
+plan equals the FP64 oracle's gate-by-gate result (complex128 <= 1e-12,
+complex64 <= 1e-5 with fidelity >= 1 - 1e-6)."""
+import numpy as np
+import pytest
+
+from oracle import fast as qf
+from oracle import qudit_oracle as qo
+from paper_2211_07918_gb300 import qudit as L
+from paper_2211_07918_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2211_07918_gb300.build import build
+    build()
+    L.load()
+
+
+def _run(dims, gates, prec, kind, psi0=None, kmax=None, dmax=None):
+    with L.Register(dims, None, prec) as r:
+        if kmax:
+            L.qd_set_tuning(r.h, L.QD_TUNE_FUSE_KMAX, kmax)
+        if dmax:
+            L.qd_set_tuning(r.h, L.QD_TUNE_FUSE_DMAX, dmax)
+        if psi0 is not None:
+            L.qd_set_amplitudes(r.h, psi0)
+        plan = L.qd_plan_create(r.h, gates, kind)
+        info = L.qd_plan_info(plan)
+        L.qd_plan_run(plan)
+        L.qd_sync(r.h)
+        L.qd_plan_destroy(plan)
+        return r.amplitudes().astype(np.complex128), info
+
+
+def _check(psi, ref, prec):
+    err = np.max(np.abs(psi - ref))
+    if prec == L.QD_C128:
+        assert err <= 1e-12, err
+    else:
+        assert err <= 1e-5, err
+        assert qo.fidelity(ref, psi) >= (1 - 1e-6) * qo.norm2(ref) ** 2
+
+
+@pytest.mark.parametrize("kind", [L.QD_PLAN_GREEDY, L.QD_PLAN_EXHAUSTIVE])
+@pytest.mark.parametrize("prec", [L.QD_C128, L.QD_C64])
+def test_fused_c0(prec, kind):
+    dims, gates = wl.circuit_c0()
+    ref = qo.run_circuit(dims, gates, mode="dense")
+    psi, info = _run(dims, gates, prec, kind)
+    _check(psi, ref, prec)
+
+
+@pytest.mark.parametrize("seed", range(10))
+@pytest.mark.parametrize("prec", [L.QD_C128, L.QD_C64])
+def test_fused_random(seed, prec):
+    rng = np.random.default_rng(900 + seed)
+    n = int(rng.integers(3, 9))
+    dims = [int(x) for x in rng.choice([2, 3, 4, 5], size=n)]
+    while qo.register_size(dims) > 50000:
+        dims.pop()
+    gates = wl.random_circuit(dims, 30, 900 + seed, wl.C0_MIX + ("U2",))
+    gates = [g for g in gates if np.prod([dims[q] for q in g.targets]) <= 32]
+    N = qo.register_size(dims)
+    psi0 = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    psi0 /= np.linalg.norm(psi0)
+    ref = qf.run_circuit(dims, gates, psi0=psi0)
+    for kind in (L.QD_PLAN_GREEDY, L.QD_PLAN_EXHAUSTIVE):
+        psi, info = _run(dims, gates, prec, kind, psi0=psi0)
+        _check(psi, ref, prec)
+    # a larger fusion limit (4 qudits, D <= 32) exercises bigger blocks
+    psi, info = _run(dims, gates, prec, L.QD_PLAN_GREEDY, psi0=psi0, kmax=4, dmax=32)
+    _check(psi, ref, prec)
+
+
+@pytest.fixture(scope="module")
+def c1_ref():
+    dims, gates = wl.circuit_c1()
+    return dims, gates, qf.run_circuit(dims, gates)
+
+
+@pytest.mark.parametrize("kind", [L.QD_PLAN_GREEDY, L.QD_PLAN_EXHAUSTIVE])
+@pytest.mark.parametrize("prec", [L.QD_C128, L.QD_C64])
+def test_fused_c1_full_size(prec, kind, c1_ref):
+    dims, gates, ref = c1_ref
+    psi, info = _run(dims, gates, prec, kind)
+    assert info["blocks"] > 0 and info["launches"] < len(gates)
+    _check(psi, ref, prec)
