@@ -129,8 +129,9 @@ int qd_set_stream(qd_reg *reg, void *stream);
  * Errors: QD_ERR_ARG for an unknown key or a negative value. */
 #define QD_TUNE_TILE_STRIDE 1
 /* QD_TUNE_FUSE_KMAX: most qudits a fused block may span (1..6, default 3).
- * QD_TUNE_FUSE_DMAX: largest dimension of a fused block (2..QD_MAX_D,
- * default 32). */
+ * QD_TUNE_FUSE_DMAX: largest dimension of a fused block: complex64 2..64
+ * (default 64; blocks with D >= 9 run on the tensor cores as split-BF16
+ * products with FP32 accumulation), complex128 2..QD_MAX_D (default 32). */
 #define QD_TUNE_FUSE_KMAX 2
 #define QD_TUNE_FUSE_DMAX 3
 int qd_set_tuning(qd_reg *reg, int32_t key, int64_t value);
@@ -198,6 +199,7 @@ int qd_plan_destroy(qd_plan *plan);
 #define QD_KCLASS_DENSE_TILE 1
 #define QD_KCLASS_MONO_DIRECT 2
 #define QD_KCLASS_MONO_TILE 3
+#define QD_KCLASS_TENSOR_BLOCK 4 /* fused block on tcgen05 (split-BF16, FP32 accumulate) */
 int qd_plan_profile(qd_plan *plan, int32_t enable);
 int qd_plan_timings(qd_plan *plan, float *ms, double *alg_bytes, int32_t *kclass);
 /* Plan, run once with direct launches (no graph capture) and release. */

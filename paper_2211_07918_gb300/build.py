@@ -27,6 +27,7 @@ SOURCES = [
     "qd_reduce.cu",
     "qd_noalloc.cu",
     "qd_fuse.cu",
+    "qd_tc.cu",
 ]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

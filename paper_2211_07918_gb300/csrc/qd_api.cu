@@ -25,6 +25,7 @@
 #include "qd_fuse.h"
 #include "qd_plan.h"
 #include "qd_reduce.h"
+#include "qd_tc.h"
 
 using namespace qd;
 
@@ -70,13 +71,14 @@ struct qd_reg {
     int32_t *dev_err = nullptr;
     int64_t tile_stride = -1;  // -1: process default
     int32_t fuse_kmax = 3;     // largest number of qudits of a fused block
-    int32_t fuse_dmax = 32;    // largest dimension of a fused block
+    int32_t fuse_dmax = -1;    // largest dimension of a fused block (-1: 64 for c64, 32 for c128)
 };
 
 struct qd_plan {
     qd_reg *reg = nullptr;
     std::vector<GatePlan> gates;
     int32_t blocks = 0;
+    void *tc_buf = nullptr;  // device: BF16 terms of every tensor-core block
     bool profile = false;
     std::vector<cudaEvent_t> events;  // launches + 1 when profiling
     bool use_graph = true;            // capture on first run, replay afterwards
@@ -89,6 +91,7 @@ struct qd_plan {
     ~qd_plan() {
         drop_graph();
         for (cudaEvent_t e : events) cudaEventDestroy(e);
+        if (tc_buf) cudaFree(tc_buf);
     }
 };
 
@@ -117,6 +120,7 @@ int reg_ok(const qd_reg *r) {
 }
 
 cudaError_t launch_plan(const qd_reg *r, const GatePlan &g) {
+    if (g.mode == Mode::Tensor) return launch_block_tc(g, r->psi, r->sm_count, r->dev_err, r->stream);
     if (r->prec == QD_C64) return launch_gate_f32(g, r->psi, r->sm_count, r->stream);
     return launch_gate_f64(g, r->psi, r->sm_count, r->stream);
 }
@@ -700,10 +704,12 @@ int qd_set_tuning(qd_reg *r, int32_t key, int64_t value) {
             if (value < 1 || value > QD_MAX_TARGETS) return fail(QD_ERR_ARG, "fusion qudit limit must be in [1, 6]");
             r->fuse_kmax = (int32_t)value;
             return QD_OK;
-        case QD_TUNE_FUSE_DMAX:
-            if (value < 2 || value > QD_MAX_D) return fail(QD_ERR_ARG, "fusion dimension limit must be in [2, QD_MAX_D]");
+        case QD_TUNE_FUSE_DMAX: {
+            const int64_t cap = r->prec == QD_C64 ? kTcMaxD : QD_MAX_D;
+            if (value < 2 || value > cap) return fail(QD_ERR_ARG, "fusion dimension limit must be in [2, 64] (c64) or [2, 32] (c128)");
             r->fuse_dmax = (int32_t)value;
             return QD_OK;
+        }
         default:
             return fail(QD_ERR_ARG, "unknown tuning key");
     }
@@ -814,7 +820,8 @@ CostFn cost_for(const qd_reg *r, int plan_kind) {
 int segments_for(const qd_reg *r, const std::vector<FuseGate> &fg, int plan_kind,
                  std::vector<std::pair<int, int>> &segs, double *model_cost) {
     const RegisterShape sh = shape_of(r);
-    const int kmax = r->fuse_kmax, dmax = r->fuse_dmax;
+    const int kmax = r->fuse_kmax;
+    const int dmax = r->fuse_dmax > 0 ? r->fuse_dmax : (r->prec == QD_C64 ? kTcMaxD : QD_MAX_D);
     CostFn cost = cost_for(r, plan_kind);
     switch (plan_kind) {
         case QD_PLAN_NONE:
@@ -835,6 +842,36 @@ int segments_for(const qd_reg *r, const std::vector<FuseGate> &fg, int plan_kind
         for (auto &sg : segs) c += segment_cost(fg, sg.first, sg.second, sh, cost);
         *model_cost = c;
     }
+    return QD_OK;
+}
+
+// Tensor-core plan of one fused block (complex64): direct group geometry over
+// the block's qudits, no controls; the BF16 terms are packed into `terms`.
+int plan_block_tc(const qd_reg *r, const FuseBlock &b, GatePlan &g, std::vector<uint16_t> &terms) {
+    g = GatePlan{};
+    g.mode = Mode::Tensor;
+    g.kind = Kind::Dense;
+    g.D = b.D;
+    g.Dp = (b.D + 7) / 8 * 8;
+    g.N = (uint64_t)r->N;
+    g.R = (uint64_t)(r->N / b.D);
+    std::vector<int> asc(b.qudits.rbegin(), b.qudits.rend());
+    std::vector<std::pair<int64_t, int64_t>> ins;
+    for (int q : asc) ins.push_back({r->s[q], r->dims[q]});
+    set_expand64(g.ex, ins);
+    for (int j = 0; j < b.D; ++j) {
+        int rem = j;
+        int64_t o = 0;
+        for (int m = (int)b.qudits.size() - 1; m >= 0; --m) {
+            const int q = b.qudits[m];
+            o += (int64_t)(rem % r->dims[q]) * r->s[q];
+            rem /= r->dims[q];
+        }
+        g.off[j] = o;
+    }
+    g.alg_bytes = 2.0 * (double)r->N * (double)r->esize;
+    terms.resize(tc_terms_bytes(g.Dp) / 2);
+    tc_pack_terms(b.M.data(), b.D, g.Dp, terms.data());
     return QD_OK;
 }
 
@@ -871,6 +908,8 @@ int qd_plan_create(qd_reg *r, const qd_gate *gates, int32_t ngates, int32_t plan
     qd_plan *p = new qd_plan();
     p->reg = r;
     p->gates.reserve(segs.size());
+    std::vector<std::vector<uint16_t>> tc_terms;
+    std::vector<int> tc_index;
     for (auto &sg : segs) {
         GatePlan g;
         if (sg.first == sg.second) {
@@ -878,8 +917,15 @@ int qd_plan_create(qd_reg *r, const qd_gate *gates, int32_t ngates, int32_t plan
             rc = prepare_gate(r, orig[sg.first], g, &noop);
             if (rc == QD_OK && noop) continue;
         } else {
-            rc = plan_block(r, build_block(fg, sg.first, sg.second, r->dims), g);
-            if (rc == QD_OK && g.D == 0) continue;
+            FuseBlock b = build_block(fg, sg.first, sg.second, r->dims);
+            if (r->prec == QD_C64 && b.D >= kTcMinD && b.D <= kTcMaxD) {
+                tc_terms.emplace_back();
+                rc = plan_block_tc(r, b, g, tc_terms.back());
+                tc_index.push_back((int)p->gates.size());
+            } else {
+                rc = plan_block(r, b, g);
+                if (rc == QD_OK && g.D == 0) continue;
+            }
             ++p->blocks;
         }
         if (rc) {
@@ -887,6 +933,27 @@ int qd_plan_create(qd_reg *r, const qd_gate *gates, int32_t ngates, int32_t plan
             return rc;
         }
         p->gates.push_back(g);
+    }
+    if (!tc_terms.empty()) {  // one device buffer for every tensor-core block's terms
+        size_t total = 0;
+        for (auto &t : tc_terms) total += (t.size() * 2 + 255) / 256 * 256;
+        if (cudaMalloc(&p->tc_buf, total) != cudaSuccess) {
+            cudaGetLastError();
+            p->tc_buf = nullptr;
+            delete p;
+            return fail(QD_ERR_OOM, "tensor-core block terms allocation failed");
+        }
+        size_t off = 0;
+        for (size_t i = 0; i < tc_terms.size(); ++i) {
+            char *dst = static_cast<char *>(p->tc_buf) + off;
+            cudaError_t e = cudaMemcpy(dst, tc_terms[i].data(), tc_terms[i].size() * 2, cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) {
+                delete p;
+                return cuda_fail(e, "tensor-core block terms upload");
+            }
+            p->gates[tc_index[i]].tc_terms = dst;
+            off += (tc_terms[i].size() * 2 + 255) / 256 * 256;
+        }
     }
     *out = p;
     return QD_OK;
@@ -991,6 +1058,7 @@ int qd_plan_timings(qd_plan *p, float *ms, double *alg_bytes, int32_t *kclass) {
         if (kclass) {
             int c = g.kind == Kind::Dense ? (g.mode == Mode::Direct ? QD_KCLASS_DENSE_DIRECT : QD_KCLASS_DENSE_TILE)
                                           : (g.mode == Mode::Direct ? QD_KCLASS_MONO_DIRECT : QD_KCLASS_MONO_TILE);
+            if (g.mode == Mode::Tensor) c = QD_KCLASS_TENSOR_BLOCK;
             kclass[i] = c | (g.D << 8);
         }
     }

@@ -69,8 +69,6 @@ inline void split_coef(double re, double im, v2<T> &hi, v2<T> &lo) {
     lo = mk<T>((T)(re - (double)hi.x), (T)(im - (double)hi.y));
 }
 
-template <typename I> using ExpandT = typename ExpandOf<I>::type;
-
 // ------------------------------------------------------------ argument blocks
 // MD is the compile-time member bound; EX says D == MD exactly; I is the index
 // type.

@@ -12,6 +12,7 @@ namespace qd {
 
 constexpr int kMaxIns = 16;   // targets + controls a gate may remove from the index space
 constexpr int kMaxD = 32;     // largest target-space dimension of a per-gate kernel
+constexpr int kMaxBlockD = 64;  // largest dimension of a fused block (tensor-core kernel)
 
 template <typename T> struct V2;
 template <> struct V2<float> { using type = float2; };
@@ -140,6 +141,8 @@ __host__ __device__ __forceinline__ uint32_t expand(uint32_t r, const Expand32 &
 template <typename I> struct ExpandOf;
 template <> struct ExpandOf<uint32_t> { using type = Expand32; };
 template <> struct ExpandOf<uint64_t> { using type = Expand64; };
+
+template <typename I> using ExpandT = typename ExpandOf<I>::type;
 
 inline Expand32 narrow(const Expand64 &e) {
     Expand32 r{};

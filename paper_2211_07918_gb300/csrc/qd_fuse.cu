@@ -125,7 +125,7 @@ FuseBlock build_block(const std::vector<FuseGate> &gates, int first, int last, c
     return b;
 }
 
-LaunchFeatures launch_features(const RegisterShape &reg, const std::vector<int> &qudits, int D, bool dense,
+LaunchFeatures launch_features(const RegisterShape &reg, const std::vector<int> &qudits, int D, int kernel,
                                double slice_fraction) {
     LaunchFeatures lf;
     for (float &v : lf.f) v = 0.f;
@@ -144,7 +144,7 @@ LaunchFeatures launch_features(const RegisterShape &reg, const std::vector<int> 
     }
     lf.f[8] = (float)std::log2((double)reg.N);
     lf.f[9] = reg.precision == 2 ? 1.f : 0.f;
-    lf.f[10] = dense ? 1.f : 0.f;
+    lf.f[10] = (float)kernel;
     lf.f[11] = (float)std::log2(slice_fraction);
     return lf;
 }
@@ -153,16 +153,24 @@ double analytic_cost(const RegisterShape &reg, const LaunchFeatures &lf) {
     const double D = std::exp2((double)lf.f[0]);
     const bool c128 = lf.f[9] > 0.5f;
     const bool dense = lf.f[10] > 0.5f;
+    const bool block = lf.f[10] > 1.5f;
     const double touched = (double)reg.N * std::exp2((double)lf.f[11]);
     const double b = c128 ? 16.0 : 8.0;
     const double t_mem = 2.0 * touched * b / 5.0e12;
     double t_cmp = 0.0;
     if (dense) {
-        // complex64 with hi+lo coefficients: 8 D FFMA per amplitude;
-        // complex128: 4 D DFMA per amplitude
-        t_cmp = c128 ? touched * 4.0 * D / 0.5e12 : touched * 8.0 * D / 3.5e13;
+        if (!c128 && block && D >= 9) {
+            // fused block on the tensor cores: 4 split-BF16 products of
+            // (2 Dp) x (2 Dp) per group, about 1.2 PFLOP/s usable
+            const double Dp = std::ceil(D / 8.0) * 8.0;
+            t_cmp = touched * 32.0 * Dp * Dp / D / 1.2e15;
+        } else {
+            // complex64 with hi+lo coefficients: 8 D FFMA per amplitude plus
+            // index work; complex128: 4 D DFMA per amplitude
+            t_cmp = c128 ? touched * 4.0 * D / 0.5e12 : touched * (8.0 * D + 24.0) / 2.0e13;
+        }
     }
-    return std::max(t_mem, t_cmp) + 2.5e-6;
+    return std::max(t_mem, t_cmp) + 4.0e-6;
 }
 
 double segment_cost(const std::vector<FuseGate> &gates, int first, int last, const RegisterShape &reg,
@@ -175,10 +183,10 @@ double segment_cost(const std::vector<FuseGate> &gates, int first, int last, con
             frac /= reg.dims[g.acting[m]];
             Dt /= reg.dims[g.acting[m]];
         }
-        return cost(launch_features(reg, g.acting, Dt, !g.mono, frac));
+        return cost(launch_features(reg, g.acting, Dt, g.mono ? kKernelMono : kKernelDense, frac));
     }
     const std::vector<int> s = union_qudits(gates, first, last);
-    return cost(launch_features(reg, s, (int)dim_of(s, reg.dims), true, 1.0));
+    return cost(launch_features(reg, s, (int)dim_of(s, reg.dims), kKernelBlock, 1.0));
 }
 
 namespace {

@@ -46,11 +46,16 @@ struct RegisterShape {
     int precision;  // 1 = complex64, 2 = complex128
 };
 
+// Kernel kind of a launch (feature 10).
+constexpr int kKernelMono = 0;   // per-gate permutation with phases
+constexpr int kKernelDense = 1;  // per-gate dense (CUDA cores)
+constexpr int kKernelBlock = 2;  // fused block (tensor cores for complex64, D >= 9)
+
 // Feature vector of a launch acting on `qudits` with target dimension D:
 // log2 D, qudit count, log2 of the (up to three) smallest strides, relative
-// positions, log2 N, precision, dense flag, log2 of the control-slice
+// positions, log2 N, precision, kernel kind, log2 of the control-slice
 // fraction.
-LaunchFeatures launch_features(const RegisterShape &reg, const std::vector<int> &qudits, int D, bool dense,
+LaunchFeatures launch_features(const RegisterShape &reg, const std::vector<int> &qudits, int D, int kernel,
                                double slice_fraction);
 
 // Analytic cost (seconds): max(HBM time, arithmetic time) + launch overhead,

@@ -8,7 +8,7 @@
 
 namespace qd {
 
-enum class Mode : int32_t { Direct = 0, Tile = 1 };
+enum class Mode : int32_t { Direct = 0, Tile = 1, Tensor = 2 };
 enum class Kind : int32_t { Dense = 0, Mono = 1 };
 
 // Largest number of amplitudes a tile-mode CTA stages in shared memory per
@@ -33,7 +33,7 @@ struct GatePlan {
     uint64_t R = 0;          // number of groups
     uint64_t base_off = 0;   // sum over controls of level * stride
     Expand64 ex{};           // group index -> flat base
-    int64_t off[kMaxD] = {}; // flat offset of local index j
+    int64_t off[kMaxBlockD] = {};  // flat offset of local index j
 
     // --- tile mode: a CTA stages DH chunks of B contiguous amplitudes -------
     uint64_t R_tiles = 0;      // number of tiles
@@ -47,13 +47,17 @@ struct GatePlan {
     FastDiv32 divG{};          // group index -> tile
     Expand32 ex_lo{};          // in-tile group index -> position inside the block
     uint32_t lo_off = 0;       // controls below the block, level * stride
-    int64_t offH[kMaxD] = {};  // flat offset of chunk h
-    int32_t smoff[kMaxD] = {}; // shared-memory offset of local index j in a tile
+    int64_t offH[kMaxBlockD] = {};  // flat offset of chunk h
+    int32_t smoff[kMaxBlockD] = {}; // shared-memory offset of local index j in a tile
 
     // --- numerics (FP64, rounded to the state precision at launch) ---------
     double U[2 * kMaxD * kMaxD] = {};  // dense: row-major D x D (re, im)
     int32_t src[kMaxD] = {};           // mono: out[i] = lam[i] * in[src[i]]
     double lam[2 * kMaxD] = {};
+
+    // --- tensor mode: fused block on tcgen05 (complex64 states) -------------
+    int32_t Dp = 0;                    // D rounded up to a multiple of 8
+    const void *tc_terms = nullptr;    // device: three BF16 terms of the real embedding
     uint32_t active = 0;               // mono: bit i set if out[i] != in[i]
     uint32_t unit = 0;                 // mono: bit i set if lam[i] == 1 exactly
 

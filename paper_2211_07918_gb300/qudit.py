@@ -262,7 +262,7 @@ def qd_plan_profile(plan: int, enable: bool = True) -> None:
     _check(load().qd_plan_profile(_vp(plan), 1 if enable else 0))
 
 
-KCLASS_NAMES = {0: "dense_direct", 1: "dense_tile", 2: "mono_direct", 3: "mono_tile"}
+KCLASS_NAMES = {0: "dense_direct", 1: "dense_tile", 2: "mono_direct", 3: "mono_tile", 4: "tensor_block"}
 
 
 def qd_plan_timings(plan: int, with_times: bool = True):

@@ -88,3 +88,49 @@ def test_fused_c1_full_size(prec, kind, c1_ref):
     psi, info = _run(dims, gates, prec, kind)
     assert info["blocks"] > 0 and info["launches"] < len(gates)
     _check(psi, ref, prec)
+
+
+def _kclasses(dims, gates, prec, kind, kmax=3, dmax=None):
+    with L.Register(dims, None, prec) as r:
+        L.qd_set_tuning(r.h, L.QD_TUNE_FUSE_KMAX, kmax)
+        if dmax:
+            L.qd_set_tuning(r.h, L.QD_TUNE_FUSE_DMAX, dmax)
+        plan = L.qd_plan_create(r.h, gates, kind)
+        _, _, kc = L.qd_plan_timings(plan, with_times=False)
+        L.qd_plan_destroy(plan)
+    return [L.kclass_name(int(c)) for c in kc]
+
+
+def test_tensor_block_d64():
+    # two dense two-qudit gates on (0,1) and (1,2) of three ququarts fuse into
+    # one D = 64 block, which runs on the tensor cores
+    rng = np.random.default_rng(3)
+    dims = [4, 4, 4, 2, 3]
+    gates = [wl.Gate("U", (0, 1), matrix=wl.haar_unitary(16, rng)),
+             wl.Gate("U", (2, 1), matrix=wl.haar_unitary(16, rng))]
+    names = _kclasses(dims, gates, L.QD_C64, L.QD_PLAN_GREEDY, 3, 64)
+    assert names == ["tensor_block_D64"], names
+    N = qo.register_size(dims)
+    psi0 = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    psi0 /= np.linalg.norm(psi0)
+    ref = qo.run_circuit(dims, gates, psi0=psi0)
+    psi, info = _run(dims, gates, L.QD_C64, L.QD_PLAN_GREEDY, psi0=psi0, kmax=3, dmax=64)
+    assert info["blocks"] == 1
+    _check(psi, ref, L.QD_C64)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_tensor_blocks_random(seed):
+    rng = np.random.default_rng(1200 + seed)
+    n = int(rng.integers(4, 9))
+    dims = [int(x) for x in rng.choice([2, 3, 4], size=n)]
+    while qo.register_size(dims) > 200000:
+        dims.pop()
+    gates = wl.random_circuit(dims, 40, 1200 + seed, wl.C0_MIX + ("U2",))
+    N = qo.register_size(dims)
+    psi0 = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    psi0 /= np.linalg.norm(psi0)
+    ref = qf.run_circuit(dims, gates, psi0=psi0)
+    for kind in (L.QD_PLAN_GREEDY, L.QD_PLAN_EXHAUSTIVE):
+        psi, info = _run(dims, gates, L.QD_C64, kind, psi0=psi0, kmax=3, dmax=64)
+        _check(psi, ref, L.QD_C64)
