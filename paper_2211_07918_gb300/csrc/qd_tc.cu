@@ -9,28 +9,38 @@
 // issued as tcgen05.mma kind::f16 (BF16 inputs, FP32 accumulation in TMEM),
 // M = 128 groups, N = K = 2 Dp (Dp = D rounded up to a multiple of 8).
 //
-// Precision (complex64 states, FP32 storage): BF16 keeps 8 mantissa bits, so
-// both operands are split into unevaluated sums of BF16 terms: the state
-// x = x1 + x2 (|x - x1 - x2| <= 2^-18 |x|, incoherent per amplitude) and the
-// matrix B = B1 + B2 + B3 (|B - B1 - B2 - B3| <= 2^-27 |B|).  Four products
-// are accumulated: B1 x1 + B2 x1 + B3 x1 + B1 x2.  The matrix applied to the
-// dominant part x1 is accurate to 2^-27, so the coherent (same for every
-// group) non-unitarity that would make the norm drift over a circuit stays
-// ~1e-8 per block; the dropped terms are below 2^-17 of each amplitude and
-// incoherent.  This is the split-operand idea of Markidis et al. (2018) and
-// Ootomo & Yokota (2022) applied with BF16 terms.
+// Precision.  The tensor cores round each accumulation step toward zero; a
+// rounded running sum loses on average about 0.36 ulp per instruction, always
+// toward zero, which shrinks every amplitude coherently (measured: 1 - F =
+// 1.5e-6 after one D = 64 block with a hi/lo split).  The kernel therefore
+// keeps every partial sum exact (the error-free splitting of Ozaki, Ogita,
+// Oishi and Rump, 2012): each state row r is scaled by 2^-e_r (e_r from the
+// row maximum) and cut into three 8-bit fixed-point slices
+//     x~ = x1 + x2 + x3 + O(2^-27),  x_s = k / 2^(9s-1),  |k| <= 256,
+// and each matrix row n likewise with its own 2^-f_n into B1 + B2 + B3.  Every
+// slice value is exact in BF16, every product of two slices is a multiple of
+// one quantum per significance level, and a level's sum stays below 2^24
+// quanta, so the tensor core accumulates it without rounding.  Three TMEM
+// accumulators hold the levels 2^0 (x1 B1), 2^-9 (x1 B2 + x2 B1) and 2^-18
+// (x1 B3 + x2 B2 + x3 B1); the epilogue adds them in FP32 with
+// round-to-nearest and rescales by 2^(e_r + f_n).  The matrix is represented
+// to 2^-27 (coherent error ~1e-8 per block), the state to 2^-27 before the
+// dropped level-2^-27 products (incoherent).
 //
 // Shared-memory operands use the no-swizzle K-major canonical layout: core
 // matrices of 8 rows x 16 bytes (8 BF16), consecutive along K at 128 B
 // (leading byte offset), 8-row groups at K*16 B (stride byte offset).
 // One CTA of 128 threads owns a tile of 128 groups per iteration: thread t
-// gathers group t, splits it to BF16 and writes row t of X1, X2; one thread
-// issues the MMAs and commits them to an mbarrier; after the (bounded) wait,
-// thread t reads TMEM lane t (its group's 2D outputs) and scatters them back.
-// Every wait is bounded; on expiry the kernel records an error, waits (bounded)
-// for its MMAs, frees its TMEM and returns.
+// gathers group t, slices it and writes row t of X1..X3; one thread issues
+// the MMAs and commits them to an mbarrier; after the (bounded) wait, thread
+// t reads TMEM lane t (its group's outputs at the three levels) and scatters
+// them back.  Every wait is bounded; on expiry the kernel records an error,
+// waits (bounded) for its MMAs, frees its TMEM and returns.
+#include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <vector>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -114,9 +124,9 @@ __device__ __forceinline__ void tmem_ld<8>(uint32_t taddr, float *o) {
 
 }  // namespace
 
-// Kernel arguments: direct-mode group geometry plus the three BF16 matrix
-// terms, already in the K-major canonical layout (B1 | B2 | B3, each
-// N x K BF16 = 2*N*K bytes), in global memory.
+// Kernel arguments: direct-mode group geometry plus the matrix slices,
+// already in the K-major canonical layout (B1 | B2 | B3, each N x K BF16 =
+// 2*N*K bytes), followed by the N row scales 2^f_n (float), in global memory.
 template <typename I>
 struct TcArgs {
     float2 *psi;
@@ -128,15 +138,28 @@ struct TcArgs {
     int32_t *err;
 };
 
+// 8-bit fixed-point slices of a value already scaled into [-1, 1]:
+// s1 = k1/2^8, s2 = k2/2^17, s3 = k3/2^26 with |k| <= 256 (exact in BF16).
+__device__ __forceinline__ void slice3(float v, __nv_bfloat16 &a, __nv_bfloat16 &b, __nv_bfloat16 &c) {
+    const float s1 = rintf(v * 256.0f) * (1.0f / 256.0f);
+    const float r1 = v - s1;
+    const float s2 = rintf(r1 * 131072.0f) * (1.0f / 131072.0f);
+    const float r2 = r1 - s2;
+    const float s3 = rintf(r2 * 67108864.0f) * (1.0f / 67108864.0f);
+    a = __float2bfloat16_rn(s1);
+    b = __float2bfloat16_rn(s2);
+    c = __float2bfloat16_rn(s3);
+}
+
 template <typename I>
 __global__ void __launch_bounds__(kTcThreads, 1) k_block_tc(const __grid_constant__ TcArgs<I> a) {
     extern __shared__ __align__(1024) unsigned char sm[];
     const uint32_t K = 2u * (uint32_t)a.Dp;  // = N
-    const uint32_t xbytes = kTcRows * K * 2u;  // one state tile (BF16)
-    const uint32_t bbytes = K * K * 2u;        // one matrix term
-    unsigned char *X1 = sm;
-    unsigned char *X2 = X1 + xbytes;
-    unsigned char *B = X2 + xbytes;  // B1 | B2 | B3
+    const uint32_t xbytes = kTcRows * K * 2u;  // one state slice (BF16)
+    const uint32_t bbytes = K * K * 2u;        // one matrix slice
+    unsigned char *X = sm;                     // X1 | X2 | X3
+    unsigned char *B = X + 3u * xbytes;        // B1 | B2 | B3
+    float *bscale = reinterpret_cast<float *>(B + 3u * bbytes);
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_base;
     __shared__ int32_t abort_flag;
@@ -144,13 +167,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_block_tc(const __grid_constan
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
     uint32_t ncols = 32;
-    while (ncols < K) ncols <<= 1;
+    while (ncols < 3u * K) ncols <<= 1;
 
-    // matrix terms: global -> shared (16-byte copies)
+    // matrix slices and row scales: global -> shared (16-byte copies)
     {
         const uint4 *src = reinterpret_cast<const uint4 *>(a.terms);
         uint4 *dst = reinterpret_cast<uint4 *>(B);
-        for (uint32_t i = tid; i < 3u * bbytes / 16u; i += kTcThreads) dst[i] = src[i];
+        const uint32_t n16 = (3u * bbytes + K * 4u + 15u) / 16u;
+        for (uint32_t i = tid; i < n16; i += kTcThreads) dst[i] = src[i];
     }
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar)) : "memory");
@@ -174,46 +198,56 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_block_tc(const __grid_constan
     uint32_t phase = 0;
     const I ntiles = (a.R + kTcRows - 1) / kTcRows;
     for (I tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        // ---- gather group tid, split to BF16 hi/lo, write rows of X1, X2
+        // ---- gather group tid: row scale 2^-e from the row maximum ...
         const I g = tile * kTcRows + tid;
         const bool valid = g < a.R;
         const I base = valid ? expand(g, a.ex) : 0;
+        float amax = 0.f;
+        if (valid)
+            for (int j = 0; j < a.D; ++j) {
+                const float2 v = a.psi[base + a.off[j]];
+                amax = fmaxf(amax, fmaxf(fabsf(v.x), fabsf(v.y)));
+            }
+        int e = 0;
+        frexpf(amax, &e);  // amax <= 2^e
+        const float inv = ldexpf(1.0f, -e);
+        // ... then the three slices of every value, written to row tid of X1..X3
         for (int c0 = 0; c0 < a.Dp; c0 += 4) {  // 4 amplitudes = 8 BF16 = one 16-byte chunk
-            __align__(16) __nv_bfloat16 h[8], l[8];
+            __align__(16) __nv_bfloat16 h1[8], h2[8], h3[8];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int j = c0 + u;
                 float2 v = make_float2(0.f, 0.f);
                 if (valid && j < a.D) v = a.psi[base + a.off[j]];
-                const __nv_bfloat16 hr = __float2bfloat16_rn(v.x), hi = __float2bfloat16_rn(v.y);
-                h[2 * u] = hr;
-                h[2 * u + 1] = hi;
-                l[2 * u] = __float2bfloat16_rn(v.x - __bfloat162float(hr));
-                l[2 * u + 1] = __float2bfloat16_rn(v.y - __bfloat162float(hi));
+                slice3(v.x * inv, h1[2 * u], h2[2 * u], h3[2 * u]);
+                slice3(v.y * inv, h1[2 * u + 1], h2[2 * u + 1], h3[2 * u + 1]);
             }
             const uint32_t o = cm_off((uint32_t)tid, (uint32_t)(2 * c0), K);
-            *reinterpret_cast<uint4 *>(X1 + o) = *reinterpret_cast<const uint4 *>(h);
-            *reinterpret_cast<uint4 *>(X2 + o) = *reinterpret_cast<const uint4 *>(l);
+            *reinterpret_cast<uint4 *>(X + o) = *reinterpret_cast<const uint4 *>(h1);
+            *reinterpret_cast<uint4 *>(X + xbytes + o) = *reinterpret_cast<const uint4 *>(h2);
+            *reinterpret_cast<uint4 *>(X + 2u * xbytes + o) = *reinterpret_cast<const uint4 *>(h3);
         }
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
         __syncthreads();
-        // ---- one thread issues B1 x1 + B2 x1 + B3 x1 + B1 x2
+        // ---- one thread issues the six slice products into three level accumulators
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            const uint32_t x1 = smem_u32(X1), x2 = smem_u32(X2), b0 = smem_u32(B);
-            uint32_t acc = 0;
+            const uint32_t x0 = smem_u32(X), b0 = smem_u32(B);
+            // (level, x slice, B slice)
+            const int pairs[6][3] = {{0, 0, 0}, {1, 0, 1}, {1, 1, 0}, {2, 0, 2}, {2, 1, 1}, {2, 2, 0}};
             const uint32_t ksteps = K / 16u;
 #pragma unroll 1
-            for (int term = 0; term < 4; ++term) {
-                const uint32_t xa = term < 3 ? x1 : x2;
-                const uint32_t bt = b0 + (uint32_t)(term < 3 ? term : 0) * bbytes;
+            for (int p = 0; p < 6; ++p) {
+                const uint32_t dcol = tmem + (uint32_t)pairs[p][0] * K;
+                const uint32_t xa = x0 + (uint32_t)pairs[p][1] * xbytes;
+                const uint32_t bt = b0 + (uint32_t)pairs[p][2] * bbytes;
+                const bool first_of_level = (p == 0 || p == 1 || p == 3);
 #pragma unroll 1
                 for (uint32_t s = 0; s < ksteps; ++s) {
                     const uint64_t ad = smem_desc(xa + s * 256u, lbo, sbo);
                     const uint64_t bd = smem_desc(bt + s * 256u, lbo, sbo);
-                    mma_bf16(tmem, ad, bd, idesc, acc);
-                    acc = 1;
+                    mma_bf16(dcol, ad, bd, idesc, (first_of_level && s == 0) ? 0u : 1u);
                 }
             }
             mma_commit(mb);
@@ -232,16 +266,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_block_tc(const __grid_constan
             mbar_wait_bounded(mb, phase ^ 1u);
             break;
         }
-        // ---- TMEM lane tid -> this group's 2D outputs -> scatter back
+        // ---- TMEM lane tid: levels 2^0, 2^-9, 2^-18 -> outputs -> scatter back
         const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+        const float escale = ldexpf(1.0f, e);
         for (int c0 = 0; c0 < a.Dp; c0 += 4) {
-            float o[8];
-            tmem_ld<8>(lane_addr + (uint32_t)(2 * c0), o);
+            float l0[8], l1[8], l2[8];
+            tmem_ld<8>(lane_addr + (uint32_t)(2 * c0), l0);
+            tmem_ld<8>(lane_addr + K + (uint32_t)(2 * c0), l1);
+            tmem_ld<8>(lane_addr + 2u * K + (uint32_t)(2 * c0), l2);
             if (valid) {
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int j = c0 + u;
-                    if (j < a.D) a.psi[base + a.off[j]] = make_float2(o[2 * u], o[2 * u + 1]);
+                    if (j < a.D) {
+                        const int n = 2 * (c0 + u);
+                        const float re = (l0[2 * u] + (l1[2 * u] + l2[2 * u])) * (escale * bscale[n]);
+                        const float im = (l0[2 * u + 1] + (l1[2 * u + 1] + l2[2 * u + 1])) * (escale * bscale[n + 1]);
+                        a.psi[base + a.off[j]] = make_float2(re, im);
+                    }
                 }
             }
         }
@@ -253,52 +295,62 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_block_tc(const __grid_constan
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(ncols) : "memory");
 }
 
-size_t tc_terms_bytes(int Dp) { return (size_t)3 * (2 * Dp) * (2 * Dp) * 2; }
+size_t tc_terms_bytes(int Dp) {
+    const size_t K = 2 * (size_t)Dp;
+    return (3 * K * K * 2 + K * 4 + 15) / 16 * 16;
+}
 
 // Host: the real embedding B (N x K, N = K = 2 Dp) of the D x D complex
-// matrix U, split into three BF16 terms in the K-major canonical layout.
+// matrix U (interleaved FP64), each row n scaled by 2^-f_n (its maximum
+// <= 2^f_n) and cut into three 8-bit fixed-point slices stored as BF16 in the
+// kernel's shared-memory layout, followed by the row scales 2^f_n (float).
 void tc_pack_terms(const double *U, int D, int Dp, uint16_t *out) {
     const int K = 2 * Dp;
     const size_t term_elems = (size_t)K * K;
-    for (size_t i = 0; i < 3 * term_elems; ++i) out[i] = 0;
+    std::memset(out, 0, tc_terms_bytes(Dp));
     auto bf16_bits = [](double x) -> uint16_t {
-        // round-to-nearest-even of the FP32 value, as __float2bfloat16_rn
+        // x is a slice value k * 2^-m with |k| <= 256: exact in FP32 and BF16
         const float f = (float)x;
         uint32_t u;
         std::memcpy(&u, &f, 4);
-        if ((u & 0x7fffffffu) > 0x7f800000u) return 0x7fc0;
-        const uint32_t lsb = (u >> 16) & 1u;
-        u += 0x7fffu + lsb;
         return (uint16_t)(u >> 16);
     };
-    auto bf16_val = [](uint16_t b) -> double {
-        uint32_t u = (uint32_t)b << 16;
-        float f;
-        std::memcpy(&f, &u, 4);
-        return (double)f;
-    };
-    for (int i = 0; i < D; ++i)
-        for (int k = 0; k < D; ++k) {
-            const double ur = U[2 * (i * D + k)], ui = U[2 * (i * D + k) + 1];
-            // rows n = 2i (re), 2i+1 (im); columns 2k (x_re), 2k+1 (x_im)
-            const double e[2][2] = {{ur, -ui}, {ui, ur}};
-            for (int p = 0; p < 2; ++p)
-                for (int q = 0; q < 2; ++q) {
-                    double rem = e[p][q];
-                    const uint32_t n = 2 * i + p, kk = 2 * k + q;
-                    const uint32_t off = cm_off(n, kk, (uint32_t)K) / 2;
-                    for (int t = 0; t < 3; ++t) {
-                        const uint16_t b = bf16_bits(rem);
-                        out[t * term_elems + off] = b;
-                        rem -= bf16_val(b);
-                    }
-                }
+    std::vector<double> row((size_t)K);
+    float *scales = reinterpret_cast<float *>(out + 3 * term_elems);
+    for (int n = 0; n < K; ++n) {
+        std::fill(row.begin(), row.end(), 0.0);
+        if (n < 2 * D) {
+            const int i = n / 2, p = n % 2;
+            for (int k = 0; k < D; ++k) {
+                const double ur = U[2 * (i * D + k)], ui = U[2 * (i * D + k) + 1];
+                // row 2i: (ur, -ui) ; row 2i+1: (ui, ur) on columns (2k, 2k+1)
+                row[2 * k] = p == 0 ? ur : ui;
+                row[2 * k + 1] = p == 0 ? -ui : ur;
+            }
         }
+        double mx = 0.0;
+        for (double v : row) mx = std::max(mx, std::fabs(v));
+        int f = 0;
+        std::frexp(mx, &f);  // mx <= 2^f
+        scales[n] = (float)std::ldexp(1.0, f);
+        for (int kk = 0; kk < K; ++kk) {
+            double v = std::ldexp(row[kk], -f);
+            const double s1 = std::nearbyint(v * 256.0) / 256.0;
+            v -= s1;
+            const double s2 = std::nearbyint(v * 131072.0) / 131072.0;
+            v -= s2;
+            const double s3 = std::nearbyint(v * 67108864.0) / 67108864.0;
+            const uint32_t off = cm_off((uint32_t)n, (uint32_t)kk, (uint32_t)K) / 2;
+            out[off] = bf16_bits(s1);
+            out[term_elems + off] = bf16_bits(s2);
+            out[2 * term_elems + off] = bf16_bits(s3);
+        }
+    }
 }
 
 int tc_smem_bytes(int Dp) {
     const int K = 2 * Dp;
-    return kTcRows * K * 2 * 2 + 3 * K * K * 2;
+    return 3 * kTcRows * K * 2 + 3 * K * K * 2 + K * 4 + 16;
 }
 
 template <typename I>
@@ -319,8 +371,11 @@ static cudaError_t launch_tc_i(const GatePlan &g, void *psi, int sm_count, int32
     if (e != cudaSuccess) return e;
     int occ = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kTcThreads, smem);
-    // TMEM: 512 columns per SM; each CTA holds at most 128
-    occ = occ < 1 ? 1 : (occ > 4 ? 4 : occ);
+    // TMEM: 512 columns per SM; each CTA holds the next power of two >= 3 N
+    int ncols = 32;
+    while (ncols < 3 * 2 * g.Dp) ncols <<= 1;
+    const int tmem_cap = 512 / ncols;
+    occ = occ < 1 ? 1 : (occ > tmem_cap ? tmem_cap : occ);
     const uint64_t tiles = (g.R + kTcRows - 1) / kTcRows;
     const uint64_t cap = (uint64_t)sm_count * occ;
     const int grid = (int)(tiles < cap ? tiles : cap);
