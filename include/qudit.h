@@ -212,6 +212,11 @@ int qd_norm(qd_reg *reg, double *out);
 /* p_i = |psi_i|^2 (FP64) for all N entries into out (QD_HOST or QD_DEVICE
  * buffer of N doubles). */
 int qd_probabilities(qd_reg *reg, double *out, int32_t where);
+/* <a|b> = sum_i conj(a_i) b_i in FP64 over two registers of equal size (the
+ * precisions may differ), into *re, *im (host).  Fidelity |<a|b>|^2 between
+ * a complex64 result and a complex128 reference stays on the device.
+ * Synchronises both streams.  Errors: QD_ERR_ARG, QD_ERR_DIM. */
+int qd_overlap(qd_reg *a, qd_reg *b, double *re, double *im);
 /* P(x_q = v), v < d_q, into the host array out[d_q].  Synchronises. */
 int qd_marginal(qd_reg *reg, int32_t q, double *out);
 /* Inclusive prefix sum of p_i (FP64, left to right) into N doubles. */

@@ -1099,6 +1099,25 @@ int qd_norm(qd_reg *r, double *out) {
     return QD_OK;
 }
 
+int qd_overlap(qd_reg *a, qd_reg *b, double *re, double *im) {
+    if (int rc = reg_ok(a)) return rc;
+    if (int rc = reg_ok(b)) return rc;
+    if (!re || !im) return fail(QD_ERR_ARG, "null output");
+    if (a->N != b->N) return fail(QD_ERR_DIM, "registers differ in size");
+    const int nb = reduce_blocks(a->sm_count);
+    double *res = a->red + (size_t)nb * 64;
+    if (b->stream != a->stream) {  // b's pending work must finish before a's stream reads it
+        QD_CUDA(cudaStreamSynchronize(b->stream));
+    }
+    QD_CUDA(overlap(a->psi, a->prec, b->psi, b->prec, (uint64_t)a->N, a->red, nb, res, a->stream));
+    double h[2];
+    QD_CUDA(cudaMemcpyAsync(h, res, sizeof(h), cudaMemcpyDeviceToHost, a->stream));
+    QD_CUDA(cudaStreamSynchronize(a->stream));
+    *re = h[0];
+    *im = h[1];
+    return QD_OK;
+}
+
 int qd_marginal(qd_reg *r, int32_t q, double *out) {
     if (int rc = reg_ok(r)) return rc;
     if (!out) return fail(QD_ERR_ARG, "null output");

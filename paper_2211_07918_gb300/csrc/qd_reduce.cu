@@ -80,6 +80,43 @@ __global__ void k_sum_partials(const double *__restrict__ part, int nb, double *
     if (threadIdx.x == 0) out[blockIdx.x] = acc;
 }
 
+// Per-block partial sums of conj(a_i) * b_i (FP64), fixed order.
+template <typename TA, typename TB>
+__global__ void __launch_bounds__(kRedBlock) k_overlap_partial(const v2<TA> *__restrict__ a, const v2<TB> *__restrict__ b,
+                                                               uint64_t N, double *__restrict__ part) {
+    __shared__ double sh[32];
+    const uint64_t step = (uint64_t)gridDim.x * blockDim.x;
+    double re = 0.0, im = 0.0;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += step) {
+        const v2<TA> x = a[i];
+        const v2<TB> y = b[i];
+        const double xr = (double)x.x, xi = (double)x.y, yr = (double)y.x, yi = (double)y.y;
+        re = fma(xr, yr, fma(xi, yi, re));
+        im = fma(xr, yi, fma(-xi, yr, im));
+    }
+    re = block_sum(re, sh);
+    im = block_sum(im, sh);
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = re;
+        part[2 * blockIdx.x + 1] = im;
+    }
+}
+
+__global__ void k_sum_pairs(const double *__restrict__ part, int nb, double *__restrict__ out) {
+    __shared__ double sh[32];
+    double re = 0.0, im = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+        re += part[2 * i];
+        im += part[2 * i + 1];
+    }
+    re = block_sum(re, sh);
+    im = block_sum(im, sh);
+    if (threadIdx.x == 0) {
+        out[0] = re;
+        out[1] = im;
+    }
+}
+
 template <typename T>
 __global__ void k_probs(const v2<T> *__restrict__ psi, uint64_t N, double *__restrict__ p) {
     const uint64_t step = (uint64_t)gridDim.x * blockDim.x;
@@ -255,6 +292,22 @@ cudaError_t probabilities(const void *psi, int prec, uint64_t N, double *out, in
     const int g = grid_for(N, 256, sm_count, 8);
     if (prec == 1) k_probs<float><<<g, 256, 0, s>>>(static_cast<const float2 *>(psi), N, out);
     else k_probs<double><<<g, 256, 0, s>>>(static_cast<const double2 *>(psi), N, out);
+    return cudaGetLastError();
+}
+
+cudaError_t overlap(const void *a, int prec_a, const void *b, int prec_b, uint64_t N, double *part, int nb,
+                    double *out_dev, cudaStream_t s) {
+    if (prec_a == 1 && prec_b == 1)
+        k_overlap_partial<float, float><<<nb, kRedBlock, 0, s>>>(static_cast<const float2 *>(a), static_cast<const float2 *>(b), N, part);
+    else if (prec_a == 1)
+        k_overlap_partial<float, double><<<nb, kRedBlock, 0, s>>>(static_cast<const float2 *>(a), static_cast<const double2 *>(b), N, part);
+    else if (prec_b == 1)
+        k_overlap_partial<double, float><<<nb, kRedBlock, 0, s>>>(static_cast<const double2 *>(a), static_cast<const float2 *>(b), N, part);
+    else
+        k_overlap_partial<double, double><<<nb, kRedBlock, 0, s>>>(static_cast<const double2 *>(a), static_cast<const double2 *>(b), N, part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_sum_pairs<<<1, 256, 0, s>>>(part, nb, out_dev);
     return cudaGetLastError();
 }
 

@@ -19,6 +19,11 @@ int reduce_blocks(int sm_count);
 cudaError_t slice_norms(const void *psi, int prec, uint64_t M, const Expand64 &ex, uint64_t slice_stride, int nslices,
                         double *part, int nb, double *out_dev, cudaStream_t s);
 
+// out_dev[0..1] = <a|b> = sum conj(a_i) b_i (FP64), for states of equal length
+// (precisions may differ).  part holds 2 * nb doubles.
+cudaError_t overlap(const void *a, int prec_a, const void *b, int prec_b, uint64_t N, double *part, int nb,
+                    double *out_dev, cudaStream_t s);
+
 // p[i] = |psi_i|^2 (FP64).
 cudaError_t probabilities(const void *psi, int prec, uint64_t N, double *out, int sm_count, cudaStream_t s);
 

@@ -74,6 +74,7 @@ _SIGS = {
     "qd_norm": [_vp, _dp],
     "qd_probabilities": [_vp, _dp, _i32],
     "qd_marginal": [_vp, _i32, _dp],
+    "qd_overlap": [_vp, _vp, _dp, _dp],
     "qd_cdf": [_vp, _dp, _i32],
     "qd_sample": [_vp, ctypes.c_uint64, _i64, _i64p],
     "qd_sample_u": [_vp, _dp, _i64, _i64p],
@@ -309,6 +310,12 @@ def qd_probabilities(reg: int, out: Optional[np.ndarray] = None, where: int = QD
         out = np.empty(_n(reg), dtype=np.float64)
     _check(load().qd_probabilities(_vp(reg), out.ctypes.data_as(_dp), QD_HOST))
     return out
+
+
+def qd_overlap(a: int, b: int) -> complex:
+    re, im = ctypes.c_double(), ctypes.c_double()
+    _check(load().qd_overlap(_vp(a), _vp(b), ctypes.byref(re), ctypes.byref(im)))
+    return complex(re.value, im.value)
 
 
 def qd_marginal(reg: int, q: int, d: int) -> np.ndarray:

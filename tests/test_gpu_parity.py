@@ -279,6 +279,22 @@ def _check_samples(got, want, u, cdf):
     assert len(bad) <= max(1, len(u) // 1000)
 
 
+@pytest.mark.parametrize("pa,pb", [(L.QD_C64, L.QD_C128), (L.QD_C128, L.QD_C128), (L.QD_C64, L.QD_C64)])
+def test_overlap(pa, pb):
+    rng = np.random.default_rng(8)
+    dims = [3, 5, 4, 7]
+    N = qo.register_size(dims)
+    a = rand_state(rng, N)
+    b = rand_state(rng, N)
+    with L.Register(dims, None, pa) as ra, L.Register(dims, None, pb) as rb:
+        L.qd_set_amplitudes(ra.h, a)
+        L.qd_set_amplitudes(rb.h, b)
+        got = L.qd_overlap(ra.h, rb.h)
+        aa = ra.amplitudes().astype(np.complex128)
+        bb = rb.amplitudes().astype(np.complex128)
+    assert abs(got - np.vdot(aa, bb)) <= 1e-13
+
+
 def test_reset_and_torch_buffer():
     torch = pytest.importorskip("torch")
     dims = [3, 5, 2]
