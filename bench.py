@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-sample-gates", type=int, default=0, help="gates in the CPU-baseline sample (0: auto)")
+    ap.add_argument("--c2-ququarts", type=int, default=12,
+                    help="ququarts of the c2 register (12: the full 2^32-amplitude case; fewer for profiling)")
     ap.add_argument("--workload", default="c1", choices=["c1", "c2"],
                     help="c1: 14 qutrits, 500 gates, per-gate kernels (default); "
                          "c2: 8 qubits + 12 ququarts (2^32 amplitudes), Haar layer + d=4 QFT + Toffoli ladder, "
@@ -234,7 +236,7 @@ def run_c2(args, rank, world, local):
     L.load()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    dims, gates = wl.circuit_c2()
+    dims, gates = wl.circuit_c2(n_ququarts=args.c2_ququarts)
     N = int(np.prod(dims))
     ngates = len(gates)
     stream = torch.cuda.Stream(device=dev)
@@ -305,7 +307,9 @@ def run_c2(args, rank, world, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": res["exhaustive"]["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD_C2, "amplitudes": N, "gates": ngates, "precision": "complex64",
+        "config": {"workload": WORKLOAD_C2 if args.c2_ququarts == 12 else
+                   f"c2 shape with {args.c2_ququarts} ququarts (profiling size)",
+                   "amplitudes": N, "gates": ngates, "precision": "complex64",
                    "l2": "inputs (34.4 GB) larger than L2", "step": "reset + fused circuit"},
         "amp_updates_per_s": value * N,
         "compare": {"fused_exhaustive": res["exhaustive"], "fused_greedy": res["greedy"],

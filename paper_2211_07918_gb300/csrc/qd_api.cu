@@ -852,7 +852,7 @@ int plan_block_tc(const qd_reg *r, const FuseBlock &b, GatePlan &g, std::vector<
     g.mode = Mode::Tensor;
     g.kind = Kind::Dense;
     g.D = b.D;
-    g.Dp = (b.D + 7) / 8 * 8;
+    g.Dp = tc_padded_dim(b.D);
     g.N = (uint64_t)r->N;
     g.R = (uint64_t)(r->N / b.D);
     std::vector<int> asc(b.qudits.rbegin(), b.qudits.rend());

@@ -12,6 +12,8 @@ namespace qd {
 constexpr int kTcMinD = 9;
 constexpr int kTcMaxD = 64;
 
+// Padded dimension of a block: D rounded up to a multiple of 8 (16 above 32).
+int tc_padded_dim(int D);
 // Bytes of the three BF16 matrix terms of a block with padded dimension Dp.
 size_t tc_terms_bytes(int Dp);
 // Pack the real embedding of the D x D complex matrix U (interleaved, FP64)
