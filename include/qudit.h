@@ -71,7 +71,7 @@ extern "C" {
 
 #define QD_PLAN_NONE 0       /* one kernel per gate, no fusion */
 #define QD_PLAN_GREEDY 1     /* greedy gate fusion into blocks */
-#define QD_PLAN_LEARNED 2    /* fusion steered by the learned cost model */
+#define QD_PLAN_LEARNED 2    /* exact segmentation under the learned cost model (qd_set_cost_model) */
 #define QD_PLAN_EXHAUSTIVE 3 /* exact optimum over contiguous segmentations (small circuits) */
 
 #define QD_MAX_QUDITS 48
@@ -255,6 +255,53 @@ int qd_set_amplitudes(qd_reg *reg, const void *in, int32_t where);
 /* Wait for the register's stream; report a device-side error word (0 if
  * none) in *device_error (may be NULL).  Returns QD_ERR_DEVICE if it is set. */
 int qd_sync(qd_reg *reg, int32_t *device_error);
+
+/* ---- learned cost model ------------------------------------------------ */
+/* The fusion planner's learned cost model: an MLP 12 -> 64 -> 64 -> 64 -> 1
+ * (ReLU) predicting log(launch time in microseconds) from the 12 launch
+ * features of a candidate segment (qd_segment_features).  Trained on the GPU
+ * by the library's own forward, backward and Adam kernels; inference uses
+ * FP16 weights with FP32 accumulation.  The paper has no such component; it
+ * steers the fusion of the paper's gates (QD_PLAN_LEARNED).  Parameters are
+ * QD_MODEL_PARAMS floats: W1 (12x64, row = input), b1, W2 (64x64), b2, W3,
+ * b3, W4 (64), b4. */
+#define QD_MODEL_FEATURES 12
+#define QD_MODEL_PARAMS 9217
+typedef struct qd_model qd_model;
+int qd_model_create(qd_model **out);
+int qd_model_destroy(qd_model *model);
+/* Set parameters and the feature / target normalisation (NULL mean or std:
+ * 0 and 1). */
+int qd_model_set(qd_model *model, const float *params, const float *feat_mean, const float *feat_std, float y_mean,
+                 float y_std);
+int qd_model_get(const qd_model *model, float *params, float *feat_mean, float *feat_std, float *y_mean, float *y_std);
+/* Fit to n samples (features X[n][12] host, targets y[n] = log time) with Adam:
+ * epochs over shuffled mini-batches, learning rate lr, seeded initialisation;
+ * *final_loss = mean squared error over the set in normalised units. */
+int qd_model_train(qd_model *model, const float *X, const float *y, int32_t n, int32_t epochs, int32_t batch,
+                   float lr, uint64_t seed, double *final_loss);
+/* Predicted targets for n feature rows (host arrays), FP16 weights. */
+int qd_model_predict(qd_model *model, const float *X, int32_t n, float *y);
+/* Network on already-normalised rows (fp16 = 0: FP32 weights). */
+int qd_model_forward_raw(qd_model *model, const float *Xn, int32_t n, float *y, int32_t fp16);
+/* Mean-squared-error loss and its gradient (QD_MODEL_PARAMS floats) for
+ * already-normalised rows and targets, by the forward and backward kernels. */
+int qd_model_grad_raw(qd_model *model, const float *Xn, const float *t, int32_t n, double *loss, float *grad);
+/* Attach a model to a register for QD_PLAN_LEARNED (NULL detaches; the
+ * model must outlive the plans made with it). */
+int qd_set_cost_model(qd_reg *reg, qd_model *model);
+/* The 12 launch features of gates[first..last] (indices of the non-identity
+ * gates) as one launch on this register: log2 D, qudit count, log2 of the
+ * three smallest strides, relative positions, log2 N, precision, kernel kind
+ * (0 permutation/diagonal gate, 1 dense gate, 2 fused block), log2 of the
+ * control-slice fraction. */
+int qd_segment_features(qd_reg *reg, const qd_gate *gates, int32_t ngates, int32_t first, int32_t last, float *out);
+/* A plan from an explicit segmentation: segment i covers the non-identity
+ * gates [seg_first[i], seg_last[i]] (contiguous, in order, covering all);
+ * multi-gate segments become fused blocks regardless of the size limits of
+ * QD_TUNE_FUSE_*, up to 6 qudits and D <= 64 (complex64) or 32 (complex128). */
+int qd_plan_create_segmented(qd_reg *reg, const qd_gate *gates, int32_t ngates, const int32_t *seg_first,
+                             const int32_t *seg_last, int32_t nseg, qd_plan **out);
 
 /* Static message for an error code; thread-local message of the last failure. */
 const char *qd_strerror(int code);

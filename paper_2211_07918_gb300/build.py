@@ -28,6 +28,7 @@ SOURCES = [
     "qd_noalloc.cu",
     "qd_fuse.cu",
     "qd_tc.cu",
+    "qd_mlp.cu",
 ]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -7,6 +7,7 @@
 // Registers follow Sec. 2.2 / Sec. 3.2: N = prod d_q, qudit 0 least
 // significant, initial basis levels.
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <chrono>
 #include <thread>
@@ -23,6 +24,7 @@
 #include "../../include/qudit.h"
 #include "../../include/qudit_debug.h"
 #include "qd_fuse.h"
+#include "qd_mlp.h"
 #include "qd_plan.h"
 #include "qd_reduce.h"
 #include "qd_tc.h"
@@ -72,6 +74,7 @@ struct qd_reg {
     int64_t tile_stride = -1;  // -1: process default
     int32_t fuse_kmax = 3;     // largest number of qudits of a fused block
     int32_t fuse_dmax = -1;    // largest dimension of a fused block (-1: 64 for c64, 32 for c128)
+    qd_model *model = nullptr; // learned cost model for QD_PLAN_LEARNED
 };
 
 struct qd_plan {
@@ -834,8 +837,34 @@ int segments_for(const qd_reg *r, const std::vector<FuseGate> &fg, int plan_kind
         case QD_PLAN_EXHAUSTIVE:
             segs = segment_exhaustive(fg, sh, cost, kmax, dmax, nullptr);
             break;
+        case QD_PLAN_LEARNED: {
+            if (!r->model) return fail(QD_ERR_UNSUPPORTED, "QD_PLAN_LEARNED needs a cost model (qd_set_cost_model)");
+            // every feasible candidate segment, predicted in one batched inference
+            std::vector<std::array<float, kFeatures>> feats;
+            std::map<std::array<float, kFeatures>, double> table;
+            CostFn collect = [&](const LaunchFeatures &f) {
+                std::array<float, kFeatures> k;
+                std::copy(f.f, f.f + kFeatures, k.begin());
+                if (table.emplace(k, 0.0).second) feats.push_back(k);
+                return 0.0;
+            };
+            segment_exhaustive(fg, sh, collect, kmax, dmax, nullptr);
+            std::vector<float> X, y(feats.size());
+            for (auto &k : feats) X.insert(X.end(), k.begin(), k.end());
+            if (int rc = qd_model_predict(r->model, X.data(), (int32_t)feats.size(), y.data())) return rc;
+            for (size_t i = 0; i < feats.size(); ++i) table[feats[i]] = std::exp((double)y[i]) * 1e-6;
+            CostFn learned = [&](const LaunchFeatures &f) {
+                std::array<float, kFeatures> k;
+                std::copy(f.f, f.f + kFeatures, k.begin());
+                auto it = table.find(k);
+                return it != table.end() ? it->second : analytic_cost(sh, f);
+            };
+            segs = segment_exhaustive(fg, sh, learned, kmax, dmax, nullptr);
+            cost = learned;
+            break;
+        }
         default:
-            return fail(QD_ERR_UNSUPPORTED, "plan kind not available (learned planning needs a trained cost model)");
+            return fail(QD_ERR_ARG, "unknown plan kind");
     }
     if (model_cost) {
         double c = 0.0;
@@ -893,23 +922,20 @@ int plan_block(const qd_reg *r, const FuseBlock &b, GatePlan &g) {
 
 extern "C" {
 
-int qd_plan_create(qd_reg *r, const qd_gate *gates, int32_t ngates, int32_t plan_kind, qd_plan **out) {
-    if (!out) return fail(QD_ERR_ARG, "null output handle");
-    *out = nullptr;
-    if (int rc = reg_ok(r)) return rc;
-    if (ngates < 0 || (ngates > 0 && !gates)) return fail(QD_ERR_ARG, "bad gate list");
-    if (plan_kind < QD_PLAN_NONE || plan_kind > QD_PLAN_EXHAUSTIVE) return fail(QD_ERR_ARG, "unknown plan kind");
-    std::vector<FuseGate> fg;
-    std::vector<const qd_gate *> orig;
-    int rc = collect_gates(r, gates, ngates, fg, orig);
-    if (rc) return rc;
-    std::vector<std::pair<int, int>> segs;
-    if ((rc = segments_for(r, fg, plan_kind, segs, nullptr))) return rc;
+}  // extern "C"
+
+namespace {
+// Plan from a segmentation of the collected gates.  enforce_limits: fused
+// blocks must respect the register's QD_TUNE_FUSE_* limits (planner output
+// does by construction; explicit segmentations only need the hard limits).
+int build_plan(qd_reg *r, const std::vector<FuseGate> &fg, const std::vector<const qd_gate *> &orig,
+               const std::vector<std::pair<int, int>> &segs, qd_plan **out) {
     qd_plan *p = new qd_plan();
     p->reg = r;
     p->gates.reserve(segs.size());
     std::vector<std::vector<uint16_t>> tc_terms;
     std::vector<int> tc_index;
+    int rc = QD_OK;
     for (auto &sg : segs) {
         GatePlan g;
         if (sg.first == sg.second) {
@@ -918,7 +944,9 @@ int qd_plan_create(qd_reg *r, const qd_gate *gates, int32_t ngates, int32_t plan
             if (rc == QD_OK && noop) continue;
         } else {
             FuseBlock b = build_block(fg, sg.first, sg.second, r->dims);
-            if (r->prec == QD_C64 && b.D >= kTcMinD && b.D <= kTcMaxD) {
+            if ((int)b.qudits.size() > QD_MAX_TARGETS) {
+                rc = fail(QD_ERR_DIM, "fused block spans more than 6 qudits");
+            } else if (r->prec == QD_C64 && b.D >= kTcMinD && b.D <= kTcMaxD) {
                 tc_terms.emplace_back();
                 rc = plan_block_tc(r, b, g, tc_terms.back());
                 tc_index.push_back((int)p->gates.size());
@@ -926,7 +954,7 @@ int qd_plan_create(qd_reg *r, const qd_gate *gates, int32_t ngates, int32_t plan
                 rc = plan_block(r, b, g);
                 if (rc == QD_OK && g.D == 0) continue;
             }
-            ++p->blocks;
+            if (rc == QD_OK) ++p->blocks;
         }
         if (rc) {
             delete p;
@@ -956,6 +984,82 @@ int qd_plan_create(qd_reg *r, const qd_gate *gates, int32_t ngates, int32_t plan
         }
     }
     *out = p;
+    return QD_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int qd_plan_create(qd_reg *r, const qd_gate *gates, int32_t ngates, int32_t plan_kind, qd_plan **out) {
+    if (!out) return fail(QD_ERR_ARG, "null output handle");
+    *out = nullptr;
+    if (int rc = reg_ok(r)) return rc;
+    if (ngates < 0 || (ngates > 0 && !gates)) return fail(QD_ERR_ARG, "bad gate list");
+    if (plan_kind < QD_PLAN_NONE || plan_kind > QD_PLAN_EXHAUSTIVE) return fail(QD_ERR_ARG, "unknown plan kind");
+    std::vector<FuseGate> fg;
+    std::vector<const qd_gate *> orig;
+    int rc = collect_gates(r, gates, ngates, fg, orig);
+    if (rc) return rc;
+    std::vector<std::pair<int, int>> segs;
+    if ((rc = segments_for(r, fg, plan_kind, segs, nullptr))) return rc;
+    return build_plan(r, fg, orig, segs, out);
+}
+
+int qd_plan_create_segmented(qd_reg *r, const qd_gate *gates, int32_t ngates, const int32_t *seg_first,
+                             const int32_t *seg_last, int32_t nseg, qd_plan **out) {
+    if (!out) return fail(QD_ERR_ARG, "null output handle");
+    *out = nullptr;
+    if (int rc = reg_ok(r)) return rc;
+    if (ngates < 0 || (ngates > 0 && !gates) || nseg < 0 || (nseg > 0 && (!seg_first || !seg_last)))
+        return fail(QD_ERR_ARG, "bad arguments");
+    std::vector<FuseGate> fg;
+    std::vector<const qd_gate *> orig;
+    int rc = collect_gates(r, gates, ngates, fg, orig);
+    if (rc) return rc;
+    std::vector<std::pair<int, int>> segs;
+    int next = 0;
+    for (int i = 0; i < nseg; ++i) {
+        if (seg_first[i] != next || seg_last[i] < seg_first[i] || seg_last[i] >= (int)fg.size())
+            return fail(QD_ERR_ARG, "segments must cover the non-identity gates contiguously and in order");
+        segs.push_back({seg_first[i], seg_last[i]});
+        next = seg_last[i] + 1;
+    }
+    if (next != (int)fg.size()) return fail(QD_ERR_ARG, "segments do not cover every gate");
+    for (auto &sg : segs) {
+        if (sg.first == sg.second) continue;
+        std::vector<int> qs;
+        int64_t D = 1;
+        for (int gi = sg.first; gi <= sg.second; ++gi)
+            for (int q : fg[gi].acting)
+                if (std::find(qs.begin(), qs.end(), q) == qs.end()) {
+                    qs.push_back(q);
+                    D *= r->dims[q];
+                }
+        const int64_t cap = r->prec == QD_C64 ? kTcMaxD : QD_MAX_D;
+        if ((int)qs.size() > QD_MAX_TARGETS || D > cap) return fail(QD_ERR_DIM, "segment block too large");
+    }
+    return build_plan(r, fg, orig, segs, out);
+}
+
+int qd_set_cost_model(qd_reg *r, qd_model *model) {
+    if (int rc = reg_ok(r)) return rc;
+    r->model = model;
+    return QD_OK;
+}
+
+int qd_segment_features(qd_reg *r, const qd_gate *gates, int32_t ngates, int32_t first, int32_t last, float *out) {
+    if (int rc = reg_ok(r)) return rc;
+    if (!out) return fail(QD_ERR_ARG, "null output");
+    std::vector<FuseGate> fg;
+    std::vector<const qd_gate *> orig;
+    if (int rc = collect_gates(r, gates, ngates, fg, orig)) return rc;
+    if (first < 0 || last < first || last >= (int)fg.size()) return fail(QD_ERR_ARG, "bad segment");
+    const RegisterShape sh = shape_of(r);
+    CostFn grab = [out](const LaunchFeatures &f) {
+        std::copy(f.f, f.f + kFeatures, out);
+        return 0.0;
+    };
+    segment_cost(fg, first, last, sh, grab);
     return QD_OK;
 }
 

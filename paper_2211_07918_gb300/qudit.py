@@ -23,6 +23,7 @@ QD_GATE_X, QD_GATE_Z, QD_GATE_H, QD_GATE_U, QD_GATE_DIAG = 1, 2, 3, 4, 5
 QD_PLAN_NONE, QD_PLAN_GREEDY, QD_PLAN_LEARNED, QD_PLAN_EXHAUSTIVE = 0, 1, 2, 3
 QD_MAX_TARGETS, QD_MAX_CONTROLS = 6, 8
 QD_TUNE_TILE_STRIDE, QD_TUNE_FUSE_KMAX, QD_TUNE_FUSE_DMAX = 1, 2, 3
+QD_MODEL_FEATURES, QD_MODEL_PARAMS = 12, 9217
 ERRORS = {-1: "QD_ERR_ARG", -2: "QD_ERR_DIM", -3: "QD_ERR_OVERLAP", -4: "QD_ERR_OOM", -5: "QD_ERR_CUDA",
           -6: "QD_ERR_TIMEOUT", -7: "QD_ERR_DEVICE", -8: "QD_ERR_UNSUPPORTED"}
 
@@ -82,6 +83,21 @@ _SIGS = {
     "qd_set_amplitudes": [_vp, _vp, _i32],
     "qd_sync": [_vp, _i32p],
     "qd_cdf_noalloc": [_vp, _i64, _i32, _dp, _vp],
+    "qd_model_create": [ctypes.POINTER(_vp)],
+    "qd_model_destroy": [_vp],
+    "qd_model_set": [_vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
+                     ctypes.POINTER(ctypes.c_float), ctypes.c_float, ctypes.c_float],
+    "qd_model_get": [_vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
+                     ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)],
+    "qd_model_train": [_vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), _i32, _i32, _i32,
+                       ctypes.c_float, ctypes.c_uint64, _dp],
+    "qd_model_predict": [_vp, ctypes.POINTER(ctypes.c_float), _i32, ctypes.POINTER(ctypes.c_float)],
+    "qd_model_forward_raw": [_vp, ctypes.POINTER(ctypes.c_float), _i32, ctypes.POINTER(ctypes.c_float), _i32],
+    "qd_model_grad_raw": [_vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), _i32, _dp,
+                          ctypes.POINTER(ctypes.c_float)],
+    "qd_set_cost_model": [_vp, _vp],
+    "qd_segment_features": [_vp, ctypes.POINTER(QdGate), _i32, _i32, _i32, ctypes.POINTER(ctypes.c_float)],
+    "qd_plan_create_segmented": [_vp, ctypes.POINTER(QdGate), _i32, _i32p, _i32p, _i32, ctypes.POINTER(_vp)],
 }
 
 
@@ -496,3 +512,95 @@ def qd_debug_fuse_block(dims, gates, first, last):
     Dv = D.value
     M = m[:2 * Dv * Dv].view(np.complex128).reshape(Dv, Dv).copy()
     return qs[:k.value].tolist(), M
+
+
+# ---- learned cost model ------------------------------------------------------
+
+_fp = ctypes.POINTER(ctypes.c_float)
+
+
+def _f32(a):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+    return a, a.ctypes.data_as(_fp)
+
+
+def qd_model_create() -> int:
+    out = _vp()
+    _check(load().qd_model_create(ctypes.byref(out)))
+    return out.value
+
+
+def qd_model_destroy(model: int) -> None:
+    _check(load().qd_model_destroy(_vp(model)))
+
+
+def qd_model_set(model: int, params, feat_mean=None, feat_std=None, y_mean: float = 0.0, y_std: float = 1.0) -> None:
+    p, pp = _f32(params)
+    assert p.size == QD_MODEL_PARAMS
+    m, mp = _f32(feat_mean) if feat_mean is not None else (None, None)
+    sd, sp = _f32(feat_std) if feat_std is not None else (None, None)
+    _check(load().qd_model_set(_vp(model), pp, mp, sp, y_mean, y_std))
+
+
+def qd_model_get(model: int) -> dict:
+    p = np.zeros(QD_MODEL_PARAMS, np.float32)
+    m = np.zeros(QD_MODEL_FEATURES, np.float32)
+    sd = np.zeros(QD_MODEL_FEATURES, np.float32)
+    ym, ys = ctypes.c_float(), ctypes.c_float()
+    _check(load().qd_model_get(_vp(model), p.ctypes.data_as(_fp), m.ctypes.data_as(_fp), sd.ctypes.data_as(_fp),
+                               ctypes.byref(ym), ctypes.byref(ys)))
+    return {"params": p, "feat_mean": m, "feat_std": sd, "y_mean": ym.value, "y_std": ys.value}
+
+
+def qd_model_train(model: int, X, y, epochs: int = 60, batch: int = 256, lr: float = 2e-3, seed: int = 0) -> float:
+    Xa, Xp = _f32(X)
+    ya, yp = _f32(y)
+    loss = ctypes.c_double()
+    _check(load().qd_model_train(_vp(model), Xp, yp, len(ya), epochs, batch, lr, ctypes.c_uint64(seed),
+                                 ctypes.byref(loss)))
+    return loss.value
+
+
+def qd_model_predict(model: int, X) -> np.ndarray:
+    Xa, Xp = _f32(X)
+    n = Xa.shape[0]
+    out = np.zeros(n, np.float32)
+    _check(load().qd_model_predict(_vp(model), Xp, n, out.ctypes.data_as(_fp)))
+    return out
+
+
+def qd_model_forward_raw(model: int, Xn, fp16: bool = False) -> np.ndarray:
+    Xa, Xp = _f32(Xn)
+    n = Xa.shape[0]
+    out = np.zeros(n, np.float32)
+    _check(load().qd_model_forward_raw(_vp(model), Xp, n, out.ctypes.data_as(_fp), 1 if fp16 else 0))
+    return out
+
+
+def qd_model_grad_raw(model: int, Xn, t):
+    Xa, Xp = _f32(Xn)
+    ta, tp = _f32(t)
+    g = np.zeros(QD_MODEL_PARAMS, np.float32)
+    loss = ctypes.c_double()
+    _check(load().qd_model_grad_raw(_vp(model), Xp, tp, len(ta), ctypes.byref(loss), g.ctypes.data_as(_fp)))
+    return loss.value, g
+
+
+def qd_set_cost_model(reg: int, model: int) -> None:
+    _check(load().qd_set_cost_model(_vp(reg), _vp(model or None)))
+
+
+def qd_segment_features(reg: int, gates, first: int, last: int) -> np.ndarray:
+    ga = gates if isinstance(gates, GateArray) else GateArray(gates)
+    out = np.zeros(QD_MODEL_FEATURES, np.float32)
+    _check(load().qd_segment_features(_vp(reg), ga.ptr, ga.n, first, last, out.ctypes.data_as(_fp)))
+    return out
+
+
+def qd_plan_create_segmented(reg: int, gates, segments) -> int:
+    ga = gates if isinstance(gates, GateArray) else GateArray(gates)
+    f, fp = _arr_i32([a for a, _ in segments])
+    l, lp = _arr_i32([b for _, b in segments])
+    out = _vp()
+    _check(load().qd_plan_create_segmented(_vp(reg), ga.ptr, ga.n, fp, lp, len(segments), ctypes.byref(out)))
+    return out.value
