@@ -45,10 +45,12 @@ def parse():
     ap.add_argument("--cpu-sample-gates", type=int, default=0, help="gates in the CPU-baseline sample (0: auto)")
     ap.add_argument("--c2-ququarts", type=int, default=12,
                     help="ququarts of the c2 register (12: the full 2^32-amplitude case; fewer for profiling)")
-    ap.add_argument("--workload", default="c1", choices=["c1", "c2"],
+    ap.add_argument("--workload", default="c1", choices=["c1", "c2", "c3"],
                     help="c1: 14 qutrits, 500 gates, per-gate kernels (default); "
                          "c2: 8 qubits + 12 ququarts (2^32 amplitudes), Haar layer + d=4 QFT + Toffoli ladder, "
-                         "fused tensor-core blocks vs the FP64 per-gate path")
+                         "fused tensor-core blocks vs the FP64 per-gate path; "
+                         "c3: 256 independent circuits (6-12 qudits, dims 2..5, 200 gates each) in one persistent "
+                         "graph-captured launch vs one graph-captured plan per circuit")
     return ap.parse_args()
 
 
@@ -328,6 +330,166 @@ def run_c2(args, rank, world, local):
     return 0
 
 
+WORKLOAD_C3 = ("256 independent random circuits, 6-12 qudits each with dims uniform in {2,3,4,5} "
+               "(2.44e8 amplitudes in total), 200 gates each (X, Z, F_d, CX_d, Haar-1, Haar-2), complex64, "
+               "one persistent graph-captured launch, FP64 probabilities of every register")
+
+
+def cpu_baseline_c3(circuits, min_seconds=10.0):
+    """The C oracle on whole circuits of the batch, in batch order, until
+    ``min_seconds`` have run; scaled to the whole batch by amplitude updates."""
+    from oracle import fast as qf
+    qf.build()
+    work_all = sum(int(np.prod(d)) * len(g) for d, g in circuits)
+    gates_all = sum(len(g) for _, g in circuits)
+    secs, work, ncirc = 0.0, 0, 0
+    for d, g in circuits:
+        t0 = time.perf_counter()
+        qf.run_circuit(d, g)
+        secs += time.perf_counter() - t0
+        work += int(np.prod(d)) * len(g)
+        ncirc += 1
+        if secs >= min_seconds:
+            break
+    est = secs * work_all / work
+    return {"value": gates_all / est, "unit": UNIT, "cores": qf.max_threads(), "kind": "oracle",
+            "sample": f"the first {ncirc} of {len(circuits)} circuits, whole, FP64 C index loop (OpenMP), "
+                      f"{secs:.1f} s, scaled to the batch by amplitude updates ({work:.3g} of {work_all:.3g})"}
+
+
+def run_c3(args, rank, world, local):
+    """Batched execution: all 256 circuits in one persistent kernel launch
+    (graph replay), against one captured plan per circuit."""
+    import torch
+
+    from paper_2211_07918_gb300 import qudit as L
+    from paper_2211_07918_gb300 import workloads as wl
+    from paper_2211_07918_gb300.build import build
+
+    build()
+    L.load()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    circuits = wl.batch_c3()
+    regs = [d for d, _ in circuits]
+    Ns = [int(np.prod(d)) for d in regs]
+    total = sum(Ns)
+    ngates = sum(len(g) for _, g in circuits)
+    amp_updates = sum(n * len(g) for n, (_, g) in zip(Ns, circuits))
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    b = L.qd_batch_create(regs, stream.cuda_stream)
+    for c, (_, g) in enumerate(circuits):
+        L.qd_batch_set_circuit(b, c, g)
+
+    def timed(run, steps, warmup):
+        for _ in range(warmup):
+            run()
+        stream.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for i in range(steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            ev[i][0].record(stream)
+            run()
+            ev[i][1].record(stream)
+        stream.synchronize()
+        return [a.elapsed_time(b_) for a, b_ in ev]
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    ms = timed(lambda: L.qd_batch_run(b), args.steps, args.warmup)
+    clocks = sampler.stop()
+    info = L.qd_batch_info(b, with_error=True)
+    # persistent-kernel time with events around it (direct launches)
+    L.qd_batch_profile(b, True)
+    kms = []
+    for _ in range(max(3, args.steps // 4)):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        L.qd_batch_run(b)
+        kms.append(L.qd_batch_timings(b)[0])
+    alg_bytes = L.qd_batch_timings(b, with_time=False)[1]
+    L.qd_batch_profile(b, False)
+    err = L.qd_batch_info(b, with_error=True)["device_error"]
+    # every 17th register's probabilities sum to 1 (parity itself is in the tests)
+    sums = [float(np.sum(L.qd_batch_probabilities(b, c, Ns[c]))) for c in range(0, len(circuits), 17)]
+
+    # e2e: a user's call sequence with host buffers: upload every circuit's
+    # gates, run, read every register's FP64 probabilities to pinned host memory
+    host = torch.empty(max(Ns), dtype=torch.float64).pin_memory().numpy()
+    d2h = 8 * total
+    h2d = sum(L.GateArray(g).matrix_bytes() for _, g in circuits)
+
+    def e2e_step():
+        for c, (_, g) in enumerate(circuits):
+            L.qd_batch_set_circuit(b, c, g)
+        L.qd_batch_run(b)
+        for c in range(len(circuits)):
+            L.qd_batch_probabilities(b, c, Ns[c], host)
+    e2e_step()
+    stream.synchronize()
+    e2e_steps = max(2, args.steps // 4)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    stream.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    L.qd_batch_destroy(b)
+
+    # comparison: one register and one captured plan per circuit, run in turn
+    per = []
+    for (d, g) in circuits:
+        r = L.qd_create(d, None, L.QD_C64, 0, 0, stream.cuda_stream)
+        per.append((r, L.qd_plan_create(r, g, L.QD_PLAN_NONE)))
+    probs = torch.empty(max(Ns), dtype=torch.float64, device=dev)
+
+    def per_circuit():
+        for r, p in per:
+            L.qd_reset(r)
+            L.qd_plan_run(p)
+            L.qd_probabilities(r, where=L.QD_DEVICE, dev_ptr=probs.data_ptr())
+    ms_per = timed(per_circuit, max(2, args.steps // 2), 2)
+    for r, p in per:
+        L.qd_plan_destroy(p)
+        L.qd_destroy(r)
+
+    ms_step = float(np.mean(ms))
+    value = world * ngates / (ms_step * 1e-3)
+    peak, peak_src = measured_peaks()
+    kmean = float(np.mean(kms))
+    achieved = alg_bytes / (kmean * 1e-3) / 1e9
+    cpu = cpu_baseline_c3(circuits) if rank == 0 and world == 1 else None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_C3, "circuits": len(circuits), "amplitudes": total, "gates": ngates,
+                   "precision": "complex64", "l2": "flushed (256 MiB write) before every timed step; "
+                   "states (1.95 GB) larger than L2",
+                   "step": "reset all registers + all circuits + FP64 probabilities of every register"},
+        "amp_updates_per_s": world * amp_updates / (ms_step * 1e-3),
+        "batch": {"items": info["items"], "device_error": max(info["device_error"], err),
+                  "prob_sums_sampled": sums, "kernel_ms": kmean, "kernel_share": kmean / ms_step},
+        "compare": {"per_circuit_plans_ms_per_step": float(np.mean(ms_per)),
+                    "per_circuit_plans_gates_per_s": world * ngates / (float(np.mean(ms_per)) * 1e-3),
+                    "batch_over_per_circuit": float(np.mean(ms_per)) / ms_step},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "k_batch", "peak_source": peak_src,
+                     "alg_bytes_per_launch": alg_bytes,
+                     "note": "large circuits run in groups whose states stay in L2; achieved can exceed HBM peak"},
+        "clocks": clocks,
+        "e2e": {"value": world * ngates / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_s * 1e3,
+                "path": "qd_batch_set_circuit x256 (host gates) + qd_batch_run + qd_batch_probabilities x256 (host)"},
+        "gpu_launches": int(args.steps * info["launches"]),
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_ours(args, rank, world, local):
     import torch
 
@@ -526,6 +688,8 @@ def main():
         return run_reference(args, rank, world)
     if args.workload == "c2":
         return run_c2(args, rank, world, local)
+    if args.workload == "c3":
+        return run_c3(args, rank, world, local)
     return run_ours(args, rank, world, local)
 
 

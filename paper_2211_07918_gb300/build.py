@@ -29,6 +29,7 @@ SOURCES = [
     "qd_fuse.cu",
     "qd_tc.cu",
     "qd_mlp.cu",
+    "qd_batch.cu",
 ]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

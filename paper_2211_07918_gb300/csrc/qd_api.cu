@@ -23,6 +23,7 @@
 
 #include "../../include/qudit.h"
 #include "../../include/qudit_debug.h"
+#include "qd_batch.h"
 #include "qd_fuse.h"
 #include "qd_mlp.h"
 #include "qd_plan.h"
@@ -1453,6 +1454,433 @@ int qd_debug_fuse_block(const int32_t *dims, int32_t n, const qd_gate *gates, in
     *k = (int32_t)b.qudits.size();
     *D = b.D;
     std::copy(b.M.begin(), b.M.end(), matrix);
+    return QD_OK;
+}
+
+// ---------------------------------------------------------------- batches
+
+}  // extern "C"
+
+struct qd_batch {
+    int32_t ncirc = 0;
+    std::vector<std::vector<int32_t>> dims;
+    std::vector<uint64_t> N, offs, basis;
+    std::vector<std::vector<BGate>> gates;          // per circuit
+    std::vector<std::vector<float2>> coef;          // per circuit (offsets local)
+    uint64_t total = 0;
+    uint32_t tile_amps = 8192;
+    int32_t ctas_per_sm = 0;
+    uint32_t small_amps = 6144;
+    uint64_t group_amps = uint64_t(1) << 23;
+    double alg_bytes = 0;
+    bool profile = false;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaStream_t stream = nullptr;
+    int sm_count = 0;
+    int32_t nitems = 0;
+    bool dirty = true;
+    // device
+    float2 *arena = nullptr;
+    double *probs = nullptr;
+    BGate *dgates = nullptr;
+    float2 *dcoef = nullptr;
+    BItem *ditems = nullptr;
+    uint64_t *doffs = nullptr, *dbasis = nullptr;
+    uint32_t *dsizes = nullptr, *dcounters = nullptr;
+    int32_t *derr = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    void free_tables() {
+        cudaFree(dgates);
+        cudaFree(dcoef);
+        cudaFree(ditems);
+        dgates = nullptr;
+        dcoef = nullptr;
+        ditems = nullptr;
+        if (exec) cudaGraphExecDestroy(exec);
+        exec = nullptr;
+    }
+    ~qd_batch() {
+        if (stream) cudaStreamSynchronize(stream);
+        else cudaDeviceSynchronize();
+        free_tables();
+        cudaFree(arena);
+        cudaFree(probs);
+        cudaFree(doffs);
+        cudaFree(dbasis);
+        cudaFree(dsizes);
+        cudaFree(dcounters);
+        cudaFree(derr);
+        if (ev0) cudaEventDestroy(ev0);
+        if (ev1) cudaEventDestroy(ev1);
+    }
+};
+
+namespace {
+
+int batch_encode(const qd_batch *b, int c, const qd_gate *gates, int32_t ngates, std::vector<BGate> &out,
+                 std::vector<float2> &coef) {
+    qd_reg r;
+    if (int rc = host_register(b->dims[c].data(), (int32_t)b->dims[c].size(), QD_C64, r)) return rc;
+    r.tile_stride = 0;  // direct geometry
+    out.clear();
+    coef.clear();
+    for (int i = 0; i < ngates; ++i) {
+        GatePlan g;
+        bool noop = false;
+        int rc = prepare_gate(&r, &gates[i], g, &noop);
+        if (rc) {
+            g_last_error = "circuit " + std::to_string(c) + " gate " + std::to_string(i) + ": " + g_last_error;
+            return rc;
+        }
+        if (noop) continue;
+        if (g.D > kBatchMaxD) return fail(QD_ERR_DIM, "batched gates need a target dimension <= 25");
+        BGate bg{};
+        bg.kind = g.kind == Kind::Dense ? 0 : 1;
+        bg.D = g.D;
+        bg.R = (uint32_t)g.R;
+        bg.base = (uint32_t)g.base_off;
+        bg.ex = narrow(g.ex);
+        for (int j = 0; j < g.D; ++j) {
+            bg.off[j] = (uint32_t)g.off[j];
+            bg.src[j] = g.src[j];
+        }
+        bg.active = g.active;
+        bg.unit = g.unit;
+        bg.coef = coef.size();
+        auto split = [&](double re, double im, float2 &hi, float2 &lo) {
+            hi = make_float2((float)re, (float)im);
+            lo = make_float2((float)(re - (double)hi.x), (float)(im - (double)hi.y));
+        };
+        if (bg.kind == 0) {
+            const int DD = g.D * g.D;
+            std::vector<float2> hi(DD), lo(DD);
+            for (int k = 0; k < DD; ++k) split(g.U[2 * k], g.U[2 * k + 1], hi[k], lo[k]);
+            coef.insert(coef.end(), hi.begin(), hi.end());
+            coef.insert(coef.end(), lo.begin(), lo.end());
+        } else {
+            std::vector<float2> hi(g.D), lo(g.D);
+            for (int k = 0; k < g.D; ++k) split(g.lam[2 * k], g.lam[2 * k + 1], hi[k], lo[k]);
+            coef.insert(coef.end(), hi.begin(), hi.end());
+            coef.insert(coef.end(), lo.begin(), lo.end());
+        }
+        out.push_back(bg);
+    }
+    return QD_OK;
+}
+
+// Upload the gate tables and build the work queue.
+int batch_prepare(qd_batch *b) {
+    b->free_tables();
+    std::vector<BGate> allg;
+    std::vector<float2> allc;
+    std::vector<int> gate0(b->ncirc);
+    for (int c = 0; c < b->ncirc; ++c) {
+        gate0[c] = (int)allg.size();
+        const uint64_t cbase = allc.size();
+        for (BGate g : b->gates[c]) {
+            g.coef += cbase;
+            allg.push_back(g);
+        }
+        allc.insert(allc.end(), b->coef[c].begin(), b->coef[c].end());
+    }
+    // Small circuits: one item each.  Large circuits: one item per tile of
+    // each gate, queued in groups of about group_amps amplitudes, level by
+    // level (gate 0 of every circuit of the group, then gate 1, ...), so that
+    // a group's states stay in L2 while its gates run.  Every item waits only
+    // on items queued before it.
+    std::vector<BItem> small, items;
+    std::vector<std::vector<int>> groups;
+    uint64_t in_group = 0;
+    double bytes = 0;
+    for (int c = 0; c < b->ncirc; ++c) {
+        const auto &gs = b->gates[c];
+        if (gs.empty()) continue;
+        if (b->N[c] <= b->small_amps) {
+            small.push_back(BItem{c, gate0[c], (int32_t)gs.size(), 0, 0, 0});
+            bytes += 16.0 * (double)b->N[c];
+            continue;
+        }
+        if (groups.empty() || in_group + b->N[c] > b->group_amps) {
+            groups.emplace_back();
+            in_group = 0;
+        }
+        groups.back().push_back(c);
+        in_group += b->N[c];
+    }
+    size_t total_tiles = 0;
+    std::vector<uint32_t> cum(b->ncirc, 0);
+    std::vector<BItem> tiles;
+    for (const auto &grp : groups) {
+        size_t maxg = 0;
+        for (int c : grp) maxg = std::max(maxg, b->gates[c].size());
+        for (size_t L = 0; L < maxg; ++L) {
+            for (int c : grp) {
+                const auto &gs = b->gates[c];
+                if (L >= gs.size()) continue;
+                const BGate &g = gs[L];
+                const uint32_t per = std::max<uint32_t>(1, b->tile_amps / (uint32_t)g.D);
+                uint32_t ntiles = 0;
+                for (uint32_t f = 0; f < g.R; f += per) {
+                    const uint32_t cnt = std::min(per, g.R - f);
+                    tiles.push_back(BItem{c, gate0[c] + (int32_t)L, 0, f, cnt, cum[c]});
+                    bytes += 16.0 * (double)cnt * (double)g.D;
+                    ++ntiles;
+                }
+                cum[c] += ntiles;
+            }
+        }
+    }
+    total_tiles = tiles.size();
+    // spread the small circuits evenly over the queue
+    size_t ns = 0;
+    for (size_t i = 0; i < total_tiles; ++i) {
+        const size_t want = (small.size() * (i + 1)) / (total_tiles + 1);
+        while (ns < small.size() && ns < want) items.push_back(small[ns++]);
+        items.push_back(tiles[i]);
+    }
+    while (ns < small.size()) items.push_back(small[ns++]);
+    b->alg_bytes = bytes;
+    b->nitems = (int32_t)items.size();
+    auto up = [&](void **dst, const void *src, size_t bytes) -> int {
+        if (bytes == 0) bytes = 16;
+        if (cudaMalloc(dst, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(QD_ERR_OOM, "batch table allocation failed");
+        }
+        if (src && cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice) != cudaSuccess)
+            return fail(QD_ERR_CUDA, "batch table upload failed");
+        return QD_OK;
+    };
+    if (int rc = up((void **)&b->dgates, allg.data(), allg.size() * sizeof(BGate))) return rc;
+    if (int rc = up((void **)&b->dcoef, allc.data(), allc.size() * sizeof(float2))) return rc;
+    if (int rc = up((void **)&b->ditems, items.data(), items.size() * sizeof(BItem))) return rc;
+    b->dirty = false;
+    return QD_OK;
+}
+
+BatchLaunch batch_desc(const qd_batch *b) {
+    BatchLaunch L;
+    L.arena = b->arena;
+    L.total = b->total;
+    L.offs = b->doffs;
+    L.basis = b->dbasis;
+    L.sizes = b->dsizes;
+    L.gates = b->dgates;
+    L.coef = b->dcoef;
+    L.items = b->ditems;
+    L.nitems = b->nitems;
+    L.ncirc = b->ncirc;
+    L.counters = b->dcounters;
+    L.err = b->derr;
+    L.probs = b->probs;
+    L.sm_count = b->sm_count;
+    L.ctas_per_sm = b->ctas_per_sm;
+    L.smem_amps = b->small_amps;
+    return L;
+}
+
+}  // namespace
+
+extern "C" {
+
+int qd_batch_create(int32_t ncirc, const int32_t *nqudits, const int32_t *dims_concat, void *stream, qd_batch **out) {
+    if (!out) return fail(QD_ERR_ARG, "null output handle");
+    *out = nullptr;
+    if (ncirc < 1 || !nqudits || !dims_concat) return fail(QD_ERR_ARG, "bad batch description");
+    qd_batch *b = new qd_batch();
+    b->ncirc = ncirc;
+    b->stream = static_cast<cudaStream_t>(stream);
+    int k = 0;
+    for (int c = 0; c < ncirc; ++c) {
+        if (nqudits[c] < 1 || nqudits[c] > QD_MAX_QUDITS) {
+            delete b;
+            return fail(QD_ERR_ARG, "bad qudit count");
+        }
+        std::vector<int32_t> d(dims_concat + k, dims_concat + k + nqudits[c]);
+        k += nqudits[c];
+        uint64_t N = 1;
+        for (int32_t x : d) {
+            if (x < 2 || x > 64) {
+                delete b;
+                return fail(QD_ERR_DIM, "qudit dimension must be in [2, 64]");
+            }
+            N *= (uint64_t)x;
+            if (N >= (uint64_t(1) << 31)) {
+                delete b;
+                return fail(QD_ERR_DIM, "a batched register must hold fewer than 2^31 amplitudes");
+            }
+        }
+        b->dims.push_back(d);
+        b->N.push_back(N);
+        b->offs.push_back(b->total);
+        b->basis.push_back(0);
+        b->total += N;
+    }
+    b->gates.assign(ncirc, {});
+    b->coef.assign(ncirc, {});
+    cudaError_t e = cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, 0);
+    int dev = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) {
+        delete b;
+        return cuda_fail(e, "device query");
+    }
+    std::vector<uint32_t> sizes(b->N.begin(), b->N.end());
+    if (cudaMalloc(&b->arena, b->total * sizeof(float2)) != cudaSuccess ||
+        cudaMalloc(&b->probs, b->total * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&b->doffs, ncirc * sizeof(uint64_t)) != cudaSuccess ||
+        cudaMalloc(&b->dbasis, ncirc * sizeof(uint64_t)) != cudaSuccess ||
+        cudaMalloc(&b->dsizes, ncirc * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMalloc(&b->dcounters, (ncirc + 1) * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMalloc(&b->derr, sizeof(int32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        delete b;
+        return fail(QD_ERR_OOM, "batch allocation failed");
+    }
+    if (cudaMemcpy(b->doffs, b->offs.data(), ncirc * sizeof(uint64_t), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->dbasis, b->basis.data(), ncirc * sizeof(uint64_t), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->dsizes, sizes.data(), ncirc * sizeof(uint32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(b->derr, 0, sizeof(int32_t)) != cudaSuccess) {
+        delete b;
+        return fail(QD_ERR_CUDA, "batch table upload failed");
+    }
+    *out = b;
+    return QD_OK;
+}
+
+int qd_batch_set_circuit(qd_batch *b, int32_t c, const qd_gate *gates, int32_t ngates) {
+    if (!b || c < 0 || c >= b->ncirc || ngates < 0 || (ngates > 0 && !gates)) return fail(QD_ERR_ARG, "bad arguments");
+    std::vector<BGate> g;
+    std::vector<float2> co;
+    if (int rc = batch_encode(b, c, gates, ngates, g, co)) return rc;
+    b->gates[c].swap(g);
+    b->coef[c].swap(co);
+    b->dirty = true;
+    return QD_OK;
+}
+
+int qd_batch_tune(qd_batch *b, int32_t key, int64_t value) {
+    if (!b) return fail(QD_ERR_ARG, "null batch");
+    switch (key) {
+        case QD_BATCH_TILE_AMPS:
+            if (value < 32 || value > (1 << 24)) return fail(QD_ERR_ARG, "tile size out of range");
+            b->tile_amps = (uint32_t)value;
+            break;
+        case QD_BATCH_CTAS_PER_SM:
+            if (value < 0 || value > 8) return fail(QD_ERR_ARG, "CTAs per SM out of range");
+            b->ctas_per_sm = (int32_t)value;
+            break;
+        case QD_BATCH_SMALL_AMPS:
+            if (value < 0 || value > 24576) return fail(QD_ERR_ARG, "shared-memory register size out of range");
+            b->small_amps = (uint32_t)value;
+            break;
+        case QD_BATCH_GROUP_AMPS:
+            if (value < 1) return fail(QD_ERR_ARG, "group size out of range");
+            b->group_amps = (uint64_t)value;
+            break;
+        default:
+            return fail(QD_ERR_ARG, "unknown batch tuning key");
+    }
+    b->dirty = true;
+    return QD_OK;
+}
+
+int qd_batch_run(qd_batch *b) {
+    if (!b) return fail(QD_ERR_ARG, "null batch");
+    if (b->dirty) {
+        if (b->stream) cudaStreamSynchronize(b->stream);
+        if (int rc = batch_prepare(b)) return rc;
+    }
+    const BatchLaunch desc = batch_desc(b);
+    if (b->profile) {
+        if (!b->ev0) {
+            QD_CUDA(cudaEventCreate(&b->ev0));
+            QD_CUDA(cudaEventCreate(&b->ev1));
+        }
+        QD_CUDA(batch_launch(desc, b->stream, b->ev0, b->ev1));
+        return QD_OK;
+    }
+    if (!b->stream) {
+        QD_CUDA(batch_launch(desc, b->stream));
+        return QD_OK;
+    }
+    if (!b->exec) {
+        QD_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = batch_launch(desc, b->stream);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(b->stream, &graph);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            return cuda_fail(e != cudaSuccess ? e : e2, "batch capture");
+        }
+        e = cudaGraphInstantiate(&b->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            b->exec = nullptr;
+            return cuda_fail(e, "batch graph instantiate");
+        }
+    }
+    QD_CUDA(cudaGraphLaunch(b->exec, b->stream));
+    return QD_OK;
+}
+
+int qd_batch_probabilities(qd_batch *b, int32_t c, double *out) {
+    if (!b || !out || c < 0 || c >= b->ncirc) return fail(QD_ERR_ARG, "bad arguments");
+    QD_CUDA(cudaMemcpyAsync(out, b->probs + b->offs[c], b->N[c] * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+    QD_CUDA(cudaStreamSynchronize(b->stream));
+    return QD_OK;
+}
+
+int qd_batch_get_amplitudes(qd_batch *b, int32_t c, void *out) {
+    if (!b || !out || c < 0 || c >= b->ncirc) return fail(QD_ERR_ARG, "bad arguments");
+    QD_CUDA(cudaMemcpyAsync(out, b->arena + b->offs[c], b->N[c] * sizeof(float2), cudaMemcpyDeviceToHost, b->stream));
+    QD_CUDA(cudaStreamSynchronize(b->stream));
+    return QD_OK;
+}
+
+int qd_batch_info(qd_batch *b, int64_t *total, int32_t *items, int32_t *launches, int32_t *device_error) {
+    if (!b) return fail(QD_ERR_ARG, "null batch");
+    if (b->dirty) {
+        if (int rc = batch_prepare(b)) return rc;
+    }
+    if (total) *total = (int64_t)b->total;
+    if (items) *items = b->nitems;
+    if (launches) *launches = 5;  // counter reset (memset), zero fill, basis ones, persistent kernel, probabilities
+    if (device_error) {
+        int32_t e = 0;
+        QD_CUDA(cudaMemcpyAsync(&e, b->derr, sizeof(int32_t), cudaMemcpyDeviceToHost, b->stream));
+        QD_CUDA(cudaStreamSynchronize(b->stream));
+        *device_error = e;
+    }
+    return QD_OK;
+}
+
+int qd_batch_profile(qd_batch *b, int32_t enable) {
+    if (!b) return fail(QD_ERR_ARG, "null batch");
+    b->profile = enable != 0;
+    return QD_OK;
+}
+
+int qd_batch_timings(qd_batch *b, float *kernel_ms, double *alg_bytes) {
+    if (!b) return fail(QD_ERR_ARG, "null batch");
+    if (alg_bytes) {
+        if (b->dirty) {
+            if (int rc = batch_prepare(b)) return rc;
+        }
+        *alg_bytes = b->alg_bytes;
+    }
+    if (kernel_ms) {
+        if (!b->profile || !b->ev1) return fail(QD_ERR_ARG, "no profiled run");
+        QD_CUDA(cudaEventSynchronize(b->ev1));
+        QD_CUDA(cudaEventElapsedTime(kernel_ms, b->ev0, b->ev1));
+    }
+    return QD_OK;
+}
+
+int qd_batch_destroy(qd_batch *b) {
+    delete b;
     return QD_OK;
 }
 

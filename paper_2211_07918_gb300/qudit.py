@@ -24,6 +24,7 @@ QD_PLAN_NONE, QD_PLAN_GREEDY, QD_PLAN_LEARNED, QD_PLAN_EXHAUSTIVE = 0, 1, 2, 3
 QD_MAX_TARGETS, QD_MAX_CONTROLS = 6, 8
 QD_TUNE_TILE_STRIDE, QD_TUNE_FUSE_KMAX, QD_TUNE_FUSE_DMAX = 1, 2, 3
 QD_MODEL_FEATURES, QD_MODEL_PARAMS = 12, 9217
+QD_BATCH_TILE_AMPS, QD_BATCH_CTAS_PER_SM, QD_BATCH_SMALL_AMPS, QD_BATCH_GROUP_AMPS = 1, 2, 3, 4
 ERRORS = {-1: "QD_ERR_ARG", -2: "QD_ERR_DIM", -3: "QD_ERR_OVERLAP", -4: "QD_ERR_OOM", -5: "QD_ERR_CUDA",
           -6: "QD_ERR_TIMEOUT", -7: "QD_ERR_DEVICE", -8: "QD_ERR_UNSUPPORTED"}
 
@@ -98,6 +99,16 @@ _SIGS = {
     "qd_set_cost_model": [_vp, _vp],
     "qd_segment_features": [_vp, ctypes.POINTER(QdGate), _i32, _i32, _i32, ctypes.POINTER(ctypes.c_float)],
     "qd_plan_create_segmented": [_vp, ctypes.POINTER(QdGate), _i32, _i32p, _i32p, _i32, ctypes.POINTER(_vp)],
+    "qd_batch_create": [_i32, _i32p, _i32p, _vp, ctypes.POINTER(_vp)],
+    "qd_batch_set_circuit": [_vp, _i32, ctypes.POINTER(QdGate), _i32],
+    "qd_batch_tune": [_vp, _i32, _i64],
+    "qd_batch_run": [_vp],
+    "qd_batch_probabilities": [_vp, _i32, _dp],
+    "qd_batch_get_amplitudes": [_vp, _i32, _vp],
+    "qd_batch_info": [_vp, _i64p, _i32p, _i32p, _i32p],
+    "qd_batch_profile": [_vp, _i32],
+    "qd_batch_timings": [_vp, ctypes.POINTER(ctypes.c_float), _dp],
+    "qd_batch_destroy": [_vp],
 }
 
 
@@ -604,3 +615,68 @@ def qd_plan_create_segmented(reg: int, gates, segments) -> int:
     out = _vp()
     _check(load().qd_plan_create_segmented(_vp(reg), ga.ptr, ga.n, fp, lp, len(segments), ctypes.byref(out)))
     return out.value
+
+
+# ---- batched persistent execution -----------------------------------------
+
+def qd_batch_create(registers: Sequence[Sequence[int]], stream: int = 0) -> int:
+    """One batch of independent registers (one dims list per circuit)."""
+    nq, nqp = _arr_i32([len(r) for r in registers])
+    dc, dcp = _arr_i32([int(d) for r in registers for d in r])
+    out = _vp()
+    _check(load().qd_batch_create(len(nq), nqp, dcp, _vp(stream or None), ctypes.byref(out)))
+    return out.value
+
+
+def qd_batch_set_circuit(batch: int, c: int, gates) -> None:
+    ga = gates if isinstance(gates, GateArray) else GateArray(gates)
+    _check(load().qd_batch_set_circuit(_vp(batch), c, ga.ptr if ga.n else None, ga.n))
+
+
+def qd_batch_tune(batch: int, key: int, value: int) -> None:
+    _check(load().qd_batch_tune(_vp(batch), key, int(value)))
+
+
+def qd_batch_run(batch: int) -> None:
+    _check(load().qd_batch_run(_vp(batch)))
+
+
+def qd_batch_info(batch: int, with_error: bool = False) -> dict:
+    t, it, la, er = _i64(), _i32(), _i32(), _i32()
+    _check(load().qd_batch_info(_vp(batch), ctypes.byref(t), ctypes.byref(it), ctypes.byref(la),
+                                ctypes.byref(er) if with_error else None))
+    d = {"total": t.value, "items": it.value, "launches": la.value}
+    if with_error:
+        d["device_error"] = er.value
+    return d
+
+
+def qd_batch_probabilities(batch: int, c: int, n: int, out: Optional[np.ndarray] = None) -> np.ndarray:
+    """FP64 probabilities of circuit c (n amplitudes) into ``out`` (float64,
+    at least n entries) or a new array."""
+    if out is None:
+        out = np.empty(n, np.float64)
+    assert out.dtype == np.float64 and out.flags.c_contiguous and out.size >= n
+    _check(load().qd_batch_probabilities(_vp(batch), c, out.ctypes.data_as(_dp)))
+    return out
+
+
+def qd_batch_get_amplitudes(batch: int, c: int, n: int) -> np.ndarray:
+    out = np.empty(n, np.complex64)
+    _check(load().qd_batch_get_amplitudes(_vp(batch), c, _vp(out.ctypes.data)))
+    return out
+
+
+def qd_batch_profile(batch: int, enable: bool = True) -> None:
+    _check(load().qd_batch_profile(_vp(batch), int(bool(enable))))
+
+
+def qd_batch_timings(batch: int, with_time: bool = True):
+    """(persistent-kernel ms of the last profiled run or None, algorithmic bytes)."""
+    ms, ab = ctypes.c_float(), ctypes.c_double()
+    _check(load().qd_batch_timings(_vp(batch), ctypes.byref(ms) if with_time else None, ctypes.byref(ab)))
+    return (ms.value if with_time else None), ab.value
+
+
+def qd_batch_destroy(batch: int) -> None:
+    _check(load().qd_batch_destroy(_vp(batch)))

@@ -1,0 +1,173 @@
+"""GPU parity of batched persistent execution (many independent circuits in
+one launch) against the FP64 oracle, circuit by circuit.
+
+Each circuit starts from |0...0> on its own register; the library returns the
+complex64 amplitudes and the FP64 probabilities of every register.  Bars:
+amplitudes <= 1e-5 max-abs and fidelity >= 1 - 1e-6 (the complex64 bar of the
+per-gate kernels); probabilities <= 2e-5 max-abs, since
+| |a|^2 - |b|^2 | <= (|a| + |b|) |a - b| <= 2 |a - b| for amplitudes of
+modulus <= 1.
+"""
+import numpy as np
+import pytest
+
+from oracle import fast as qf
+from oracle import qudit_oracle as qo
+from paper_2211_07918_gb300 import qudit as L
+from paper_2211_07918_gb300 import workloads as wl
+from paper_2211_07918_gb300.workloads import Gate
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-5
+FID64 = 1 - 1e-6
+TOLP = 2e-5
+MIX = wl.C0_MIX + ("U2",)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2211_07918_gb300.build import build
+    build()
+    L.load()
+
+
+def mixed_batch(seed, count, ngates, nmin=2, nmax=7, dims=(2, 3, 4, 5)):
+    out = []
+    for c in range(count):
+        rng = np.random.default_rng(seed + c)
+        n = int(rng.integers(nmin, nmax + 1))
+        d = [int(x) for x in rng.choice(dims, size=n)]
+        out.append((d, [wl.random_gate(rng, d, MIX) for _ in range(ngates)]))
+    return out
+
+
+def run_batch(circuits, tune=(), stream=0, runs=1):
+    b = L.qd_batch_create([d for d, _ in circuits], stream)
+    try:
+        for key, val in tune:
+            L.qd_batch_tune(b, key, val)
+        for c, (_, gates) in enumerate(circuits):
+            L.qd_batch_set_circuit(b, c, gates)
+        for _ in range(runs):
+            L.qd_batch_run(b)
+        info = L.qd_batch_info(b, with_error=True)
+        amps, probs = [], []
+        for c, (d, _) in enumerate(circuits):
+            N = int(np.prod(d))
+            amps.append(L.qd_batch_get_amplitudes(b, c, N).astype(np.complex128))
+            probs.append(L.qd_batch_probabilities(b, c, N))
+        return amps, probs, info
+    finally:
+        L.qd_batch_destroy(b)
+
+
+def check_circuit(dims, gates, psi, p):
+    ref = qf.run_circuit(dims, gates)
+    err = float(np.max(np.abs(psi - ref)))
+    assert err <= TOL64, err
+    assert qo.fidelity(ref, psi) >= FID64
+    assert float(np.max(np.abs(p - qo.probabilities(ref)))) <= TOLP
+
+
+# Register sizes span 4 .. 5^7 = 78,125 amplitudes: with the default limit of
+# 6,144 amplitudes in shared memory, both the whole-circuit items and the
+# tiled gate items run.
+@pytest.mark.parametrize("tune", [
+    (),
+    ((L.QD_BATCH_SMALL_AMPS, 0),),                                  # every circuit tiled
+    ((L.QD_BATCH_SMALL_AMPS, 0), (L.QD_BATCH_TILE_AMPS, 100)),      # many ragged tiles
+    ((L.QD_BATCH_SMALL_AMPS, 24576), (L.QD_BATCH_CTAS_PER_SM, 1)),  # mostly in shared memory
+    ((L.QD_BATCH_TILE_AMPS, 1 << 20), (L.QD_BATCH_CTAS_PER_SM, 3)),  # one tile per gate
+], ids=["default", "all_tiled", "ragged_tiles", "smem_1cta", "one_tile"])
+def test_batch_vs_oracle(tune):
+    circuits = mixed_batch(9100, 24, 40)
+    amps, probs, info = run_batch(circuits, tune)
+    assert info["device_error"] == 0
+    for (d, g), psi, p in zip(circuits, amps, probs):
+        check_circuit(d, g, psi, p)
+
+
+def test_batch_graph_replay_on_stream():
+    torch = pytest.importorskip("torch")
+    circuits = mixed_batch(9200, 12, 30, nmin=3, nmax=8)
+    s = torch.cuda.Stream()
+    amps1, probs1, info = run_batch(circuits, stream=s.cuda_stream, runs=1)
+    amps3, probs3, info3 = run_batch(circuits, stream=s.cuda_stream, runs=3)
+    assert info["device_error"] == 0 and info3["device_error"] == 0
+    for (d, g), a1, a3, p1, p3 in zip(circuits, amps1, amps3, probs1, probs3):
+        # every run restarts from |0...0>: replaying the graph changes nothing
+        assert np.array_equal(a1, a3) and np.array_equal(p1, p3)
+        check_circuit(d, g, a3, p3)
+
+
+def test_batch_edge_cases():
+    # empty circuits, a one-qudit register, a gate whose control level is
+    # never occupied, and set_circuit replacing an earlier gate list
+    circuits = [
+        ([3, 2], []),
+        ([5], [Gate("H", (0,))]),
+        ([2, 3, 4], [Gate("X", (2,), (0,), (1,), 1)]),  # control qudit 0 stays at level 0
+        ([4, 4, 4, 4, 4, 4, 4], [Gate("H", (q,)) for q in range(7)] + [Gate("Z", (3,), param=1)]),
+    ]
+    b = L.qd_batch_create([d for d, _ in circuits])
+    try:
+        L.qd_batch_set_circuit(b, 1, [Gate("X", (0,), param=2)])
+        for c, (_, g) in enumerate(circuits):
+            L.qd_batch_set_circuit(b, c, g)
+        L.qd_batch_run(b)
+        assert L.qd_batch_info(b, with_error=True)["device_error"] == 0
+        for c, (d, g) in enumerate(circuits):
+            N = int(np.prod(d))
+            check_circuit(d, g, L.qd_batch_get_amplitudes(b, c, N).astype(np.complex128),
+                          L.qd_batch_probabilities(b, c, N))
+    finally:
+        L.qd_batch_destroy(b)
+
+
+def test_batch_rejections():
+    with pytest.raises(L.QuditError) as e:
+        L.qd_batch_create([[2] * 31])  # 2^31 amplitudes
+    assert e.value.code == -2
+    with pytest.raises(L.QuditError):
+        L.qd_batch_create([[3, 1]])
+    b = L.qd_batch_create([[6, 6], [2, 2]])
+    try:
+        rng = np.random.default_rng(5)
+        with pytest.raises(L.QuditError) as e:  # D = 36 > 25
+            L.qd_batch_set_circuit(b, 0, [Gate("U", (0, 1), matrix=wl.haar_unitary(36, rng))])
+        assert e.value.code == -2
+        with pytest.raises(L.QuditError):
+            L.qd_batch_set_circuit(b, 2, [])
+        with pytest.raises(L.QuditError):
+            L.qd_batch_set_circuit(b, 1, [Gate("X", (0,), (0,), (1,), 1)])  # control == target
+        with pytest.raises(L.QuditError):
+            L.qd_batch_tune(b, 99, 1)
+    finally:
+        L.qd_batch_destroy(b)
+
+
+def test_batch_c3_full():
+    """The full batching workload (256 circuits, 6-12 qudits of dims 2..5,
+    200 gates each, ~2.4e8 amplitudes in total): every register's FP64
+    probabilities sum to 1, and every circuit of at most 2e5 amplitudes
+    matches the oracle amplitude by amplitude."""
+    circuits = wl.batch_c3()
+    amps_needed = {c for c, (d, _) in enumerate(circuits) if int(np.prod(d)) <= 200_000}
+    assert len(amps_needed) >= 16
+    b = L.qd_batch_create([d for d, _ in circuits])
+    try:
+        for c, (_, g) in enumerate(circuits):
+            L.qd_batch_set_circuit(b, c, g)
+        L.qd_batch_run(b)
+        info = L.qd_batch_info(b, with_error=True)
+        assert info["device_error"] == 0
+        assert info["total"] == sum(int(np.prod(d)) for d, _ in circuits)
+        for c, (d, g) in enumerate(circuits):
+            N = int(np.prod(d))
+            p = L.qd_batch_probabilities(b, c, N)
+            assert abs(float(np.sum(p)) - 1.0) <= 1e-5, (c, float(np.sum(p)))
+            if c in amps_needed:
+                check_circuit(d, g, L.qd_batch_get_amplitudes(b, c, N).astype(np.complex128), p)
+    finally:
+        L.qd_batch_destroy(b)
