@@ -259,29 +259,39 @@ int qd_sync(qd_reg *reg, int32_t *device_error);
 /* ---- batched persistent execution -------------------------------------- */
 /* Many independent circuits, each on its own register (dims of uneven count
  * and value), complex64 states in one device arena, run by one persistent
- * kernel launch: small circuits are simulated whole in one CTA's shared
- * memory, large ones gate by gate in tiles ordered by per-circuit completion
- * counters (bounded waits).  Each run resets every register to |0...0>,
- * applies all circuits and writes the FP64 probabilities of every amplitude;
- * on a non-default stream the sequence is captured into a CUDA graph on the
- * first run and replayed afterwards.  Gates: target dimension <= 25; every
- * register holds fewer than 2^31 amplitudes. */
+ * kernel launch (QuDiet Sec. 2.2 registers, Sec. 2.1.2 / 3.4 gates).  Each
+ * circuit is cut into segments of consecutive gates whose acting qudits fit a
+ * shared-memory tile; a work item loads tiles of a segment, applies all its
+ * gates in shared memory and writes them back (a register of at most
+ * QD_BATCH_SMALL_AMPS amplitudes is one segment and one tile).  Items of a
+ * circuit's later segments wait on per-circuit completion counters (bounded
+ * waits).  Each run resets every register to |0...0>, applies all circuits
+ * and writes the FP64 probabilities of every amplitude; on a non-default
+ * stream the sequence is captured into a CUDA graph on the first run and
+ * replayed afterwards.  Gates: target dimension <= 25, acting qudits (targets
+ * and controls) spanning <= 24576 amplitudes; every register holds fewer than
+ * 2^31 amplitudes.  The batch owns its device memory; the caller owns every
+ * host buffer passed in. */
 typedef struct qd_batch qd_batch;
-#define QD_BATCH_TILE_AMPS 1   /* amplitudes per tile of a large circuit's gate (default 8192) */
+#define QD_BATCH_TILE_AMPS 1   /* largest shared-memory tile of a large circuit's segment (default 4096) */
 #define QD_BATCH_CTAS_PER_SM 2 /* persistent CTAs per SM (0: as many as fit; default 0) */
 #define QD_BATCH_SMALL_AMPS 3  /* largest register simulated whole in shared memory (default 6144) */
 #define QD_BATCH_GROUP_AMPS 4  /* large circuits are queued in groups of about this many amplitudes,
                                   level by level within a group, so that a group's states stay in L2
                                   (default 2^23) */
+#define QD_BATCH_TILES_PER_ITEM 5 /* tiles one work item processes (default 1) */
 /* ncirc registers; register c has nqudits[c] qudits whose dims follow in
  * dims_concat (concatenated in circuit order).  stream: cudaStream_t as void*. */
 int qd_batch_create(int32_t ncirc, const int32_t *nqudits, const int32_t *dims_concat, void *stream, qd_batch **out);
-/* Set (replace) the gate list of circuit c.  Errors as for qd_plan_create,
- * plus QD_ERR_DIM for a target dimension above 25. */
+/* Set (replace) the gate list of circuit c (copied; identity gates dropped).
+ * Errors as for qd_plan_create, plus QD_ERR_DIM for a target dimension above
+ * 25 and QD_ERR_UNSUPPORTED for acting qudits spanning more than 24576
+ * amplitudes. */
 int qd_batch_set_circuit(qd_batch *b, int32_t c, const qd_gate *gates, int32_t ngates);
 /* Launch-shape tuning (QD_BATCH_*), used by the autotuner; takes effect at the next run. */
 int qd_batch_tune(qd_batch *b, int32_t key, int64_t value);
-/* Run every circuit once (asynchronous on the batch's stream). */
+/* Run every circuit once (asynchronous on the batch's stream).  The first
+ * run after a change segments and uploads every circuit. */
 int qd_batch_run(qd_batch *b);
 /* FP64 probabilities / amplitudes of circuit c after the last run (host
  * buffers of N_c entries; synchronise the stream). */
@@ -292,8 +302,8 @@ int qd_batch_get_amplitudes(qd_batch *b, int32_t c, void *out);
 int qd_batch_info(qd_batch *b, int64_t *total_amplitudes, int32_t *items, int32_t *launches, int32_t *device_error);
 /* Profiling mode: runs launch directly (no graph) with CUDA events around the
  * persistent kernel.  qd_batch_timings (synchronises) returns that kernel's
- * time in the last run and its algorithmic HBM bytes (every item reads and
- * writes the amplitudes it updates once, 16 bytes per complex64 amplitude). */
+ * time in the last run and its algorithmic bytes (every segment reads and
+ * writes its register once: 16 bytes per complex64 amplitude per segment). */
 int qd_batch_profile(qd_batch *b, int32_t enable);
 int qd_batch_timings(qd_batch *b, float *kernel_ms, double *alg_bytes);
 int qd_batch_destroy(qd_batch *b);

@@ -46,6 +46,22 @@ int qd_debug_segment_cost(const int32_t *dims, int32_t n, int32_t precision, con
  * complex, row-major; cap doubles available). */
 int qd_debug_fuse_block(const int32_t *dims, int32_t n, const qd_gate *gates, int32_t ngates, int32_t first,
                         int32_t last, int32_t *qudits, int32_t *k, int32_t *D, double *matrix, int64_t cap);
+/* Batched execution replay (host only, no device).  Builds the batch of
+ * ncirc registers (as qd_batch_create; circuit c's ngates[c] gates follow one
+ * another in `gates`), applies the tuning tune[0..4) = tile amplitudes, small
+ * register limit, group amplitudes, tiles per item (a negative entry keeps
+ * the default; tune may be NULL), encodes the segments, tiles, local gate
+ * geometry and work queue exactly as a run does, and replays the queue in
+ * order on the host in FP64 with the kernel's index arithmetic, from every
+ * register at |0...0>.  amps (2 * total doubles) receives the final states
+ * (interleaved complex, arena order); info (5 int64): segments, work items,
+ * largest tile, algorithmic bytes, and an error mask: 1 an item waits on a
+ * later one, 2 a tile index leaves its register, 4 a segment's tiles do not
+ * cover the register exactly once, 8 a gate index leaves its tile, 16 a
+ * chunk of gate descriptors overflows its shared-memory area or is
+ * misaligned. */
+int qd_debug_batch_emulate(int32_t ncirc, const int32_t *nqudits, const int32_t *dims_concat, const qd_gate *gates,
+                           const int32_t *ngates, const int64_t *tune, double *amps, int64_t *info);
 #ifdef __cplusplus
 }
 #endif

@@ -7,6 +7,7 @@
 // Registers follow Sec. 2.2 / Sec. 3.2: N = prod d_q, qudit 0 least
 // significant, initial basis levels.
 #include <algorithm>
+#include <complex>
 #include <array>
 #include <atomic>
 #include <chrono>
@@ -1462,17 +1463,27 @@ int qd_debug_fuse_block(const int32_t *dims, int32_t n, const qd_gate *gates, in
 }  // extern "C"
 
 struct qd_batch {
+    // One validated gate of a circuit: acting qudits and its matrix over the
+    // targets (as in the per-gate path), kept until the batch is prepared.
+    struct Stored {
+        Acting a;
+        std::vector<double> M;
+        bool diag = false;
+        uint64_t mask = 0;  // acting qudits (targets and controls)
+    };
     int32_t ncirc = 0;
     std::vector<std::vector<int32_t>> dims;
     std::vector<uint64_t> N, offs, basis;
-    std::vector<std::vector<BGate>> gates;          // per circuit
-    std::vector<std::vector<float2>> coef;          // per circuit (offsets local)
+    std::vector<std::vector<Stored>> circ;
     uint64_t total = 0;
-    uint32_t tile_amps = 8192;
+    uint32_t tile_amps = 4096;
     int32_t ctas_per_sm = 0;
     uint32_t small_amps = 6144;
     uint64_t group_amps = uint64_t(1) << 23;
+    uint32_t tiles_per_item = 1;
+    uint32_t tile_cap = 0;
     double alg_bytes = 0;
+    int64_t nsegs = 0;
     bool profile = false;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     cudaStream_t stream = nullptr;
@@ -1482,24 +1493,36 @@ struct qd_batch {
     // device
     float2 *arena = nullptr;
     double *probs = nullptr;
+    BSeg *dsegs = nullptr;
+    BChunk *dchunks = nullptr;
     BGate *dgates = nullptr;
     float2 *dcoef = nullptr;
+    uint32_t *dhoff = nullptr;
     BItem *ditems = nullptr;
     uint64_t *doffs = nullptr, *dbasis = nullptr;
-    uint32_t *dsizes = nullptr, *dcounters = nullptr;
+    uint32_t *dcounters = nullptr;
     int32_t *derr = nullptr;
     cudaGraphExec_t exec = nullptr;
+    bool host_only = false;  // host-side replay object: owns no device memory
     void free_tables() {
+        if (host_only) return;
+        cudaFree(dsegs);
+        cudaFree(dchunks);
         cudaFree(dgates);
         cudaFree(dcoef);
+        cudaFree(dhoff);
         cudaFree(ditems);
+        dsegs = nullptr;
+        dchunks = nullptr;
         dgates = nullptr;
         dcoef = nullptr;
+        dhoff = nullptr;
         ditems = nullptr;
         if (exec) cudaGraphExecDestroy(exec);
         exec = nullptr;
     }
     ~qd_batch() {
+        if (host_only) return;
         if (stream) cudaStreamSynchronize(stream);
         else cudaDeviceSynchronize();
         free_tables();
@@ -1507,7 +1530,6 @@ struct qd_batch {
         cudaFree(probs);
         cudaFree(doffs);
         cudaFree(dbasis);
-        cudaFree(dsizes);
         cudaFree(dcounters);
         cudaFree(derr);
         if (ev0) cudaEventDestroy(ev0);
@@ -1517,144 +1539,335 @@ struct qd_batch {
 
 namespace {
 
-int batch_encode(const qd_batch *b, int c, const qd_gate *gates, int32_t ngates, std::vector<BGate> &out,
-                 std::vector<float2> &coef) {
+uint64_t mask_product(const std::vector<int32_t> &dims, uint64_t m) {
+    uint64_t p = 1;
+    for (size_t q = 0; q < dims.size(); ++q)
+        if ((m >> q) & 1u) p *= (uint64_t)dims[q];
+    return p;
+}
+
+// Greedy segmentation of circuit c: a segment starts with one gate's acting
+// qudits S and takes the following gates while the union stays within tmax
+// amplitudes; S is then widened with the lowest remaining qudits that still
+// fit (longer contiguous runs, fewer tiles), and the following gates acting
+// inside the widened S join the segment.
+std::vector<std::pair<int, uint64_t>> batch_segments(const qd_batch *b, int c, uint64_t tmax) {
+    const auto &gs = b->circ[c];
+    const auto &d = b->dims[c];
+    std::vector<std::pair<int, uint64_t>> segs;  // (first gate, S)
+    size_t i = 0;
+    while (i < gs.size()) {
+        uint64_t S = gs[i].mask;
+        size_t j = i + 1;
+        while (j < gs.size() && mask_product(d, S | gs[j].mask) <= tmax) S |= gs[j++].mask;
+        uint64_t P = mask_product(d, S);
+        for (size_t q = 0; q < d.size(); ++q)
+            if (!((S >> q) & 1u) && P * (uint64_t)d[q] <= tmax) {
+                S |= uint64_t(1) << q;
+                P *= (uint64_t)d[q];
+            }
+        while (j < gs.size() && (gs[j].mask & ~S) == 0) ++j;
+        segs.push_back({(int)i, S});
+        i = j;
+    }
+    return segs;
+}
+
+// FP32 hi + lo pairs of a gate's coefficients (dense: D x D, else D phases),
+// appended to coef: ncoef hi entries, then ncoef lo entries.
+void split_coef(const GatePlan &g, BGate &bg, std::vector<float2> &coef) {
+    const int n = bg.kind == 0 ? g.D * g.D : g.D;
+    const double *src = bg.kind == 0 ? g.U : g.lam;
+    bg.ncoef = (uint32_t)n;
+    std::vector<float2> hi(n), lo(n);
+    for (int k = 0; k < n; ++k) {
+        const double re = src[2 * k], im = src[2 * k + 1];
+        hi[k] = make_float2((float)re, (float)im);
+        lo[k] = make_float2((float)(re - (double)hi[k].x), (float)(im - (double)hi[k].y));
+    }
+    coef.insert(coef.end(), hi.begin(), hi.end());
+    coef.insert(coef.end(), lo.begin(), lo.end());
+}
+
+// Expansion with adjacent insertions merged into runs (at most kBExMax).
+bool merge_expand(const Expand64 &e, BEx &out) {
+    out = BEx{};
+    uint64_t dv[kMaxIns], sp[kMaxIns];
+    int n = 0;
+    for (int k = 0; k < e.n; ++k) {
+        if (n > 0 && e.div[k].d == sp[n - 1]) {
+            sp[n - 1] = e.span[k];
+        } else {
+            dv[n] = e.div[k].d;
+            sp[n] = e.span[k];
+            ++n;
+        }
+    }
+    if (n > kBExMax) return false;
+    out.n = n;
+    for (int k = 0; k < n; ++k) {
+        out.div[k] = make_fastdiv32((uint32_t)dv[k]);
+        out.span[k] = (uint32_t)sp[k];
+    }
+    return true;
+}
+
+struct BatchTables {
+    std::vector<BSeg> segs;
+    std::vector<BChunk> chunks;
+    std::vector<BGate> gates;
+    std::vector<float2> coef;
+    std::vector<uint32_t> hoff;
+    std::vector<BItem> items;
+    uint32_t cap = 1;
+    double bytes = 0;
+};
+
+// Segment and encode every circuit; build the work queue (host only).
+int batch_tables(const qd_batch *b, BatchTables &tb) {
+    std::vector<BSeg> &segs = tb.segs;
+    std::vector<BChunk> &chunks = tb.chunks;
+    std::vector<BGate> &gates = tb.gates;
+    std::vector<float2> &coef = tb.coef;
+    std::vector<uint32_t> &hoff = tb.hoff;
+    std::vector<std::vector<int>> cseg(b->ncirc);  // segment indices per circuit
+    uint32_t cap = 0;
+    double bytes = 0;
+    for (int c = 0; c < b->ncirc; ++c) {
+        const auto &d = b->dims[c];
+        const int n = (int)d.size();
+        const uint64_t N = b->N[c];
+        const uint64_t tmax = N <= b->small_amps ? N : std::min<uint64_t>(N, b->tile_amps);
+        const auto parts = batch_segments(b, c, tmax);
+        for (size_t p = 0; p < parts.size(); ++p) {
+            const int first = parts[p].first;
+            const int last = p + 1 < parts.size() ? parts[p + 1].first : (int)b->circ[c].size();
+            const uint64_t S = parts[p].second;
+            const uint64_t T = mask_product(d, S);
+            if (T > kBatchMaxTile)
+                return fail(QD_ERR_UNSUPPORTED, "a batched gate acts on more than 24576 amplitudes of its register");
+            cap = std::max<uint32_t>(cap, (uint32_t)T);
+            // local register over S (ascending qudits) and the position map
+            std::vector<int32_t> ldims;
+            int pos[QD_MAX_QUDITS];
+            for (int q = 0; q < n; ++q)
+                if ((S >> q) & 1u) {
+                    pos[q] = (int)ldims.size();
+                    ldims.push_back(d[q]);
+                }
+            qd_reg lr;
+            if (int rc = host_register(ldims.data(), (int32_t)ldims.size(), QD_C64, lr)) return rc;
+            lr.tile_stride = 0;  // direct geometry
+            BSeg sg{};
+            sg.chunk0 = (int32_t)chunks.size();
+            const size_t gate_begin = gates.size();
+            BChunk ch{(int32_t)gates.size(), 0, (uint32_t)coef.size(), 0};
+            for (int gi = first; gi < last; ++gi) {
+                const auto &st = b->circ[c][gi];
+                Acting la = st.a;
+                for (int m = 0; m < la.k; ++m) la.t[m] = pos[la.t[m]];
+                for (int m = 0; m < la.nc; ++m) la.c[m] = pos[la.c[m]];
+                GatePlan g;
+                bool noop = false;
+                if (int rc = plan_gate(&lr, st.M.data(), la, st.diag, g, &noop)) return rc;
+                if (noop) continue;
+                BGate bg{};
+                bg.kind = g.kind == Kind::Dense ? 0 : 1;
+                bg.D = g.D;
+                bg.R = (uint32_t)g.R;
+                bg.base = (uint32_t)g.base_off;
+                if (!merge_expand(g.ex, bg.ex)) return fail(QD_ERR_UNSUPPORTED, "gate geometry exceeds the batch descriptor");
+                for (int j = 0; j < g.D; ++j) {
+                    bg.off[j] = (uint16_t)g.off[j];
+                    bg.src[j] = (int8_t)g.src[j];
+                }
+                bg.active = g.active;
+                bg.unit = g.unit;
+                std::vector<float2> gc;
+                split_coef(g, bg, gc);
+                // close the chunk when this gate's descriptor and coefficients would overflow it
+                const size_t need = (size_t)(ch.ngates + 1) * sizeof(BGate) + (ch.ncoef + gc.size()) * sizeof(float2);
+                if (ch.ngates > 0 && need > kBatchDescBytes) {
+                    chunks.push_back(ch);
+                    ch = BChunk{(int32_t)gates.size(), 0, (uint32_t)coef.size(), 0};
+                }
+                bg.coef = ch.ncoef;
+                ch.ncoef += (uint32_t)gc.size();
+                ch.ngates += 1;
+                coef.insert(coef.end(), gc.begin(), gc.end());
+                gates.push_back(bg);
+            }
+            if (ch.ngates > 0) chunks.push_back(ch);
+            sg.nchunks = (int32_t)chunks.size() - sg.chunk0;
+            if (gates.size() == gate_begin) continue;
+            // tile geometry: contiguous low block, run table over the rest of S
+            int m = 0;
+            uint64_t B = 1;
+            while (m < n && ((S >> m) & 1u)) B *= (uint64_t)d[m++];
+            sg.T = (uint32_t)T;
+            sg.B = (uint32_t)B;
+            sg.divB = make_fastdiv32((uint32_t)B);
+            sg.hoff = (uint32_t)hoff.size();
+            const uint64_t H = T / B;
+            {
+                // strides of the register
+                std::vector<uint64_t> s(n + 1, 1);
+                for (int q = 0; q < n; ++q) s[q + 1] = s[q] * (uint64_t)d[q];
+                for (uint64_t h = 0; h < H; ++h) {
+                    uint64_t rem = h, o = 0;
+                    for (int q = m; q < n; ++q)
+                        if ((S >> q) & 1u) {
+                            o += (rem % (uint64_t)d[q]) * s[q];
+                            rem /= (uint64_t)d[q];
+                        }
+                    hoff.push_back((uint32_t)o);
+                }
+                // tile index -> flat base: insert a zero digit run at every run of S
+                std::vector<std::pair<int64_t, int64_t>> runs;
+                for (int q = 0; q < n;) {
+                    if (!((S >> q) & 1u)) {
+                        ++q;
+                        continue;
+                    }
+                    int e = q;
+                    int64_t dp = 1;
+                    while (e < n && ((S >> e) & 1u)) dp *= d[e++];
+                    runs.push_back({(int64_t)s[q], dp});
+                    q = e;
+                }
+                Expand64 ex64;
+                set_expand64(ex64, runs);
+                sg.ex = narrow(ex64);
+            }
+            sg.ntiles = (uint32_t)(N / T);
+            cseg[c].push_back((int)segs.size());
+            segs.push_back(sg);
+            bytes += 16.0 * (double)N;
+        }
+    }
+    // Work queue.  Circuits in groups of about group_amps amplitudes (a
+    // circuit no larger than small_amps is one item); within a group items
+    // go segment level by segment level, so that a group's states stay in L2.
+    std::vector<BItem> &items = tb.items;
+    std::vector<int> grp;
+    uint64_t in_group = 0;
+    auto flush_group = [&]() {
+        size_t maxs = 0;
+        for (int c : grp) maxs = std::max(maxs, cseg[c].size());
+        std::vector<uint32_t> cum(grp.size(), 0);
+        for (size_t L = 0; L < maxs; ++L)
+            for (size_t k = 0; k < grp.size(); ++k) {
+                const int c = grp[k];
+                if (L >= cseg[c].size()) continue;
+                const BSeg &sg = segs[cseg[c][L]];
+                for (uint32_t t = 0; t < sg.ntiles; t += b->tiles_per_item) {
+                    const uint32_t cnt = std::min(b->tiles_per_item, sg.ntiles - t);
+                    items.push_back(BItem{c, cseg[c][L], t, cnt, cum[k], 0});
+                }
+                cum[k] += sg.ntiles;
+            }
+        grp.clear();
+        in_group = 0;
+    };
+    for (int c = 0; c < b->ncirc; ++c) {
+        if (cseg[c].empty()) continue;
+        if (!grp.empty() && in_group + b->N[c] > b->group_amps) flush_group();
+        grp.push_back(c);
+        in_group += b->N[c];
+    }
+    if (!grp.empty()) flush_group();
+    tb.cap = std::max<uint32_t>(cap, 1);
+    tb.bytes = bytes;
+    return QD_OK;
+}
+
+// Segment, encode and upload every circuit; build the work queue.
+int batch_prepare(qd_batch *b) {
+    b->free_tables();
+    BatchTables tb;
+    if (int rc = batch_tables(b, tb)) return rc;
+    const auto &segs = tb.segs;
+    const auto &gates = tb.gates;
+    const auto &coef = tb.coef;
+    const auto &hoff = tb.hoff;
+    const auto &items = tb.items;
+    b->nitems = (int32_t)items.size();
+    b->nsegs = (int64_t)segs.size();
+    b->alg_bytes = tb.bytes;
+    b->tile_cap = tb.cap;
+    auto up = [&](void **dst, const void *src, size_t bytes_) -> int {
+        if (bytes_ == 0) bytes_ = 16;
+        if (cudaMalloc(dst, bytes_) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(QD_ERR_OOM, "batch table allocation failed");
+        }
+        if (src && cudaMemcpy(*dst, src, bytes_, cudaMemcpyHostToDevice) != cudaSuccess)
+            return fail(QD_ERR_CUDA, "batch table upload failed");
+        return QD_OK;
+    };
+    if (int rc = up((void **)&b->dsegs, segs.data(), segs.size() * sizeof(BSeg))) return rc;
+    if (int rc = up((void **)&b->dchunks, tb.chunks.data(), tb.chunks.size() * sizeof(BChunk))) return rc;
+    if (int rc = up((void **)&b->dgates, gates.data(), gates.size() * sizeof(BGate))) return rc;
+    if (int rc = up((void **)&b->dcoef, coef.data(), coef.size() * sizeof(float2))) return rc;
+    if (int rc = up((void **)&b->dhoff, hoff.data(), hoff.size() * sizeof(uint32_t))) return rc;
+    if (int rc = up((void **)&b->ditems, items.data(), items.size() * sizeof(BItem))) return rc;
+    b->dirty = false;
+    return QD_OK;
+}
+
+// Validate and keep circuit c's gates (host only).
+int batch_store(qd_batch *b, int32_t c, const qd_gate *gates, int32_t ngates) {
     qd_reg r;
     if (int rc = host_register(b->dims[c].data(), (int32_t)b->dims[c].size(), QD_C64, r)) return rc;
-    r.tile_stride = 0;  // direct geometry
-    out.clear();
-    coef.clear();
+    r.tile_stride = 0;
+    std::vector<qd_batch::Stored> out;
     for (int i = 0; i < ngates; ++i) {
+        qd_batch::Stored st;
+        const qd_gate *gt = &gates[i];
+        int rc = validate(&r, gt->targets, gt->k, gt->controls, gt->ctrl_levels, gt->nc, st.a);
+        if (!rc) rc = gate_matrix(&r, gt, st.a, st.M, &st.diag);
         GatePlan g;
         bool noop = false;
-        int rc = prepare_gate(&r, &gates[i], g, &noop);
+        if (!rc) rc = plan_gate(&r, st.M.data(), st.a, st.diag, g, &noop);
         if (rc) {
             g_last_error = "circuit " + std::to_string(c) + " gate " + std::to_string(i) + ": " + g_last_error;
             return rc;
         }
         if (noop) continue;
-        if (g.D > kBatchMaxD) return fail(QD_ERR_DIM, "batched gates need a target dimension <= 25");
-        BGate bg{};
-        bg.kind = g.kind == Kind::Dense ? 0 : 1;
-        bg.D = g.D;
-        bg.R = (uint32_t)g.R;
-        bg.base = (uint32_t)g.base_off;
-        bg.ex = narrow(g.ex);
-        for (int j = 0; j < g.D; ++j) {
-            bg.off[j] = (uint32_t)g.off[j];
-            bg.src[j] = g.src[j];
-        }
-        bg.active = g.active;
-        bg.unit = g.unit;
-        bg.coef = coef.size();
-        auto split = [&](double re, double im, float2 &hi, float2 &lo) {
-            hi = make_float2((float)re, (float)im);
-            lo = make_float2((float)(re - (double)hi.x), (float)(im - (double)hi.y));
-        };
-        if (bg.kind == 0) {
-            const int DD = g.D * g.D;
-            std::vector<float2> hi(DD), lo(DD);
-            for (int k = 0; k < DD; ++k) split(g.U[2 * k], g.U[2 * k + 1], hi[k], lo[k]);
-            coef.insert(coef.end(), hi.begin(), hi.end());
-            coef.insert(coef.end(), lo.begin(), lo.end());
-        } else {
-            std::vector<float2> hi(g.D), lo(g.D);
-            for (int k = 0; k < g.D; ++k) split(g.lam[2 * k], g.lam[2 * k + 1], hi[k], lo[k]);
-            coef.insert(coef.end(), hi.begin(), hi.end());
-            coef.insert(coef.end(), lo.begin(), lo.end());
-        }
-        out.push_back(bg);
+        if (st.a.D > kBatchMaxD) return fail(QD_ERR_DIM, "batched gates need a target dimension <= 25");
+        for (int m = 0; m < st.a.k; ++m) st.mask |= uint64_t(1) << st.a.t[m];
+        for (int m = 0; m < st.a.nc; ++m) st.mask |= uint64_t(1) << st.a.c[m];
+        if (mask_product(b->dims[c], st.mask) > kBatchMaxTile)
+            return fail(QD_ERR_UNSUPPORTED, "a batched gate acts on more than 24576 amplitudes of its register");
+        out.push_back(std::move(st));
     }
+    b->circ[c].swap(out);
+    b->dirty = true;
     return QD_OK;
 }
 
-// Upload the gate tables and build the work queue.
-int batch_prepare(qd_batch *b) {
-    b->free_tables();
-    std::vector<BGate> allg;
-    std::vector<float2> allc;
-    std::vector<int> gate0(b->ncirc);
-    for (int c = 0; c < b->ncirc; ++c) {
-        gate0[c] = (int)allg.size();
-        const uint64_t cbase = allc.size();
-        for (BGate g : b->gates[c]) {
-            g.coef += cbase;
-            allg.push_back(g);
+// Registers of the batch: dims, sizes and arena offsets (host only).
+int batch_shape(qd_batch *b, int32_t ncirc, const int32_t *nqudits, const int32_t *dims_concat) {
+    b->ncirc = ncirc;
+    int k = 0;
+    for (int c = 0; c < ncirc; ++c) {
+        if (nqudits[c] < 1 || nqudits[c] > QD_MAX_QUDITS) return fail(QD_ERR_ARG, "bad qudit count");
+        std::vector<int32_t> d(dims_concat + k, dims_concat + k + nqudits[c]);
+        k += nqudits[c];
+        uint64_t N = 1;
+        for (int32_t x : d) {
+            if (x < 2 || x > 64) return fail(QD_ERR_DIM, "qudit dimension must be in [2, 64]");
+            N *= (uint64_t)x;
+            if (N >= (uint64_t(1) << 31))
+                return fail(QD_ERR_DIM, "a batched register must hold fewer than 2^31 amplitudes");
         }
-        allc.insert(allc.end(), b->coef[c].begin(), b->coef[c].end());
+        b->dims.push_back(d);
+        b->N.push_back(N);
+        b->offs.push_back(b->total);
+        b->basis.push_back(0);
+        b->total += N;
     }
-    // Small circuits: one item each.  Large circuits: one item per tile of
-    // each gate, queued in groups of about group_amps amplitudes, level by
-    // level (gate 0 of every circuit of the group, then gate 1, ...), so that
-    // a group's states stay in L2 while its gates run.  Every item waits only
-    // on items queued before it.
-    std::vector<BItem> small, items;
-    std::vector<std::vector<int>> groups;
-    uint64_t in_group = 0;
-    double bytes = 0;
-    for (int c = 0; c < b->ncirc; ++c) {
-        const auto &gs = b->gates[c];
-        if (gs.empty()) continue;
-        if (b->N[c] <= b->small_amps) {
-            small.push_back(BItem{c, gate0[c], (int32_t)gs.size(), 0, 0, 0});
-            bytes += 16.0 * (double)b->N[c];
-            continue;
-        }
-        if (groups.empty() || in_group + b->N[c] > b->group_amps) {
-            groups.emplace_back();
-            in_group = 0;
-        }
-        groups.back().push_back(c);
-        in_group += b->N[c];
-    }
-    size_t total_tiles = 0;
-    std::vector<uint32_t> cum(b->ncirc, 0);
-    std::vector<BItem> tiles;
-    for (const auto &grp : groups) {
-        size_t maxg = 0;
-        for (int c : grp) maxg = std::max(maxg, b->gates[c].size());
-        for (size_t L = 0; L < maxg; ++L) {
-            for (int c : grp) {
-                const auto &gs = b->gates[c];
-                if (L >= gs.size()) continue;
-                const BGate &g = gs[L];
-                const uint32_t per = std::max<uint32_t>(1, b->tile_amps / (uint32_t)g.D);
-                uint32_t ntiles = 0;
-                for (uint32_t f = 0; f < g.R; f += per) {
-                    const uint32_t cnt = std::min(per, g.R - f);
-                    tiles.push_back(BItem{c, gate0[c] + (int32_t)L, 0, f, cnt, cum[c]});
-                    bytes += 16.0 * (double)cnt * (double)g.D;
-                    ++ntiles;
-                }
-                cum[c] += ntiles;
-            }
-        }
-    }
-    total_tiles = tiles.size();
-    // spread the small circuits evenly over the queue
-    size_t ns = 0;
-    for (size_t i = 0; i < total_tiles; ++i) {
-        const size_t want = (small.size() * (i + 1)) / (total_tiles + 1);
-        while (ns < small.size() && ns < want) items.push_back(small[ns++]);
-        items.push_back(tiles[i]);
-    }
-    while (ns < small.size()) items.push_back(small[ns++]);
-    b->alg_bytes = bytes;
-    b->nitems = (int32_t)items.size();
-    auto up = [&](void **dst, const void *src, size_t bytes) -> int {
-        if (bytes == 0) bytes = 16;
-        if (cudaMalloc(dst, bytes) != cudaSuccess) {
-            cudaGetLastError();
-            return fail(QD_ERR_OOM, "batch table allocation failed");
-        }
-        if (src && cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice) != cudaSuccess)
-            return fail(QD_ERR_CUDA, "batch table upload failed");
-        return QD_OK;
-    };
-    if (int rc = up((void **)&b->dgates, allg.data(), allg.size() * sizeof(BGate))) return rc;
-    if (int rc = up((void **)&b->dcoef, allc.data(), allc.size() * sizeof(float2))) return rc;
-    if (int rc = up((void **)&b->ditems, items.data(), items.size() * sizeof(BItem))) return rc;
-    b->dirty = false;
+    b->circ.assign(ncirc, {});
     return QD_OK;
 }
 
@@ -1664,9 +1877,11 @@ BatchLaunch batch_desc(const qd_batch *b) {
     L.total = b->total;
     L.offs = b->doffs;
     L.basis = b->dbasis;
-    L.sizes = b->dsizes;
+    L.segs = b->dsegs;
+    L.chunks = b->dchunks;
     L.gates = b->dgates;
     L.coef = b->dcoef;
+    L.hoff = b->dhoff;
     L.items = b->ditems;
     L.nitems = b->nitems;
     L.ncirc = b->ncirc;
@@ -1675,7 +1890,7 @@ BatchLaunch batch_desc(const qd_batch *b) {
     L.probs = b->probs;
     L.sm_count = b->sm_count;
     L.ctas_per_sm = b->ctas_per_sm;
-    L.smem_amps = b->small_amps;
+    L.tile_cap = b->tile_cap;
     return L;
 }
 
@@ -1688,50 +1903,22 @@ int qd_batch_create(int32_t ncirc, const int32_t *nqudits, const int32_t *dims_c
     *out = nullptr;
     if (ncirc < 1 || !nqudits || !dims_concat) return fail(QD_ERR_ARG, "bad batch description");
     qd_batch *b = new qd_batch();
-    b->ncirc = ncirc;
     b->stream = static_cast<cudaStream_t>(stream);
-    int k = 0;
-    for (int c = 0; c < ncirc; ++c) {
-        if (nqudits[c] < 1 || nqudits[c] > QD_MAX_QUDITS) {
-            delete b;
-            return fail(QD_ERR_ARG, "bad qudit count");
-        }
-        std::vector<int32_t> d(dims_concat + k, dims_concat + k + nqudits[c]);
-        k += nqudits[c];
-        uint64_t N = 1;
-        for (int32_t x : d) {
-            if (x < 2 || x > 64) {
-                delete b;
-                return fail(QD_ERR_DIM, "qudit dimension must be in [2, 64]");
-            }
-            N *= (uint64_t)x;
-            if (N >= (uint64_t(1) << 31)) {
-                delete b;
-                return fail(QD_ERR_DIM, "a batched register must hold fewer than 2^31 amplitudes");
-            }
-        }
-        b->dims.push_back(d);
-        b->N.push_back(N);
-        b->offs.push_back(b->total);
-        b->basis.push_back(0);
-        b->total += N;
+    if (int rc = batch_shape(b, ncirc, nqudits, dims_concat)) {
+        delete b;
+        return rc;
     }
-    b->gates.assign(ncirc, {});
-    b->coef.assign(ncirc, {});
-    cudaError_t e = cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, 0);
     int dev = 0;
-    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) {
         delete b;
         return cuda_fail(e, "device query");
     }
-    std::vector<uint32_t> sizes(b->N.begin(), b->N.end());
     if (cudaMalloc(&b->arena, b->total * sizeof(float2)) != cudaSuccess ||
         cudaMalloc(&b->probs, b->total * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&b->doffs, ncirc * sizeof(uint64_t)) != cudaSuccess ||
         cudaMalloc(&b->dbasis, ncirc * sizeof(uint64_t)) != cudaSuccess ||
-        cudaMalloc(&b->dsizes, ncirc * sizeof(uint32_t)) != cudaSuccess ||
         cudaMalloc(&b->dcounters, (ncirc + 1) * sizeof(uint32_t)) != cudaSuccess ||
         cudaMalloc(&b->derr, sizeof(int32_t)) != cudaSuccess) {
         cudaGetLastError();
@@ -1740,7 +1927,6 @@ int qd_batch_create(int32_t ncirc, const int32_t *nqudits, const int32_t *dims_c
     }
     if (cudaMemcpy(b->doffs, b->offs.data(), ncirc * sizeof(uint64_t), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(b->dbasis, b->basis.data(), ncirc * sizeof(uint64_t), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(b->dsizes, sizes.data(), ncirc * sizeof(uint32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(b->derr, 0, sizeof(int32_t)) != cudaSuccess) {
         delete b;
         return fail(QD_ERR_CUDA, "batch table upload failed");
@@ -1751,20 +1937,14 @@ int qd_batch_create(int32_t ncirc, const int32_t *nqudits, const int32_t *dims_c
 
 int qd_batch_set_circuit(qd_batch *b, int32_t c, const qd_gate *gates, int32_t ngates) {
     if (!b || c < 0 || c >= b->ncirc || ngates < 0 || (ngates > 0 && !gates)) return fail(QD_ERR_ARG, "bad arguments");
-    std::vector<BGate> g;
-    std::vector<float2> co;
-    if (int rc = batch_encode(b, c, gates, ngates, g, co)) return rc;
-    b->gates[c].swap(g);
-    b->coef[c].swap(co);
-    b->dirty = true;
-    return QD_OK;
+    return batch_store(b, c, gates, ngates);
 }
 
 int qd_batch_tune(qd_batch *b, int32_t key, int64_t value) {
     if (!b) return fail(QD_ERR_ARG, "null batch");
     switch (key) {
         case QD_BATCH_TILE_AMPS:
-            if (value < 32 || value > (1 << 24)) return fail(QD_ERR_ARG, "tile size out of range");
+            if (value < 1 || value > (int64_t)kBatchMaxTile) return fail(QD_ERR_ARG, "tile size out of range");
             b->tile_amps = (uint32_t)value;
             break;
         case QD_BATCH_CTAS_PER_SM:
@@ -1772,12 +1952,16 @@ int qd_batch_tune(qd_batch *b, int32_t key, int64_t value) {
             b->ctas_per_sm = (int32_t)value;
             break;
         case QD_BATCH_SMALL_AMPS:
-            if (value < 0 || value > 24576) return fail(QD_ERR_ARG, "shared-memory register size out of range");
+            if (value < 0 || value > (int64_t)kBatchMaxTile) return fail(QD_ERR_ARG, "shared-memory register size out of range");
             b->small_amps = (uint32_t)value;
             break;
         case QD_BATCH_GROUP_AMPS:
             if (value < 1) return fail(QD_ERR_ARG, "group size out of range");
             b->group_amps = (uint64_t)value;
+            break;
+        case QD_BATCH_TILES_PER_ITEM:
+            if (value < 1 || value > 4096) return fail(QD_ERR_ARG, "tiles per item out of range");
+            b->tiles_per_item = (uint32_t)value;
             break;
         default:
             return fail(QD_ERR_ARG, "unknown batch tuning key");
@@ -1806,6 +1990,7 @@ int qd_batch_run(qd_batch *b) {
         return QD_OK;
     }
     if (!b->exec) {
+        batch_occupancy(b->tile_cap);  // sets the kernel's shared-memory attribute outside the capture
         QD_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
         cudaError_t e = batch_launch(desc, b->stream);
         cudaGraph_t graph = nullptr;
@@ -1843,11 +2028,12 @@ int qd_batch_get_amplitudes(qd_batch *b, int32_t c, void *out) {
 int qd_batch_info(qd_batch *b, int64_t *total, int32_t *items, int32_t *launches, int32_t *device_error) {
     if (!b) return fail(QD_ERR_ARG, "null batch");
     if (b->dirty) {
+        if (b->stream) cudaStreamSynchronize(b->stream);
         if (int rc = batch_prepare(b)) return rc;
     }
     if (total) *total = (int64_t)b->total;
     if (items) *items = b->nitems;
-    if (launches) *launches = 5;  // counter reset (memset), zero fill, basis ones, persistent kernel, probabilities
+    if (launches) *launches = b->nitems > 0 ? 4 : 3;  // zero fill, basis ones, persistent kernel, probabilities
     if (device_error) {
         int32_t e = 0;
         QD_CUDA(cudaMemcpyAsync(&e, b->derr, sizeof(int32_t), cudaMemcpyDeviceToHost, b->stream));
@@ -1867,6 +2053,7 @@ int qd_batch_timings(qd_batch *b, float *kernel_ms, double *alg_bytes) {
     if (!b) return fail(QD_ERR_ARG, "null batch");
     if (alg_bytes) {
         if (b->dirty) {
+            if (b->stream) cudaStreamSynchronize(b->stream);
             if (int rc = batch_prepare(b)) return rc;
         }
         *alg_bytes = b->alg_bytes;
@@ -1881,6 +2068,125 @@ int qd_batch_timings(qd_batch *b, float *kernel_ms, double *alg_bytes) {
 
 int qd_batch_destroy(qd_batch *b) {
     delete b;
+    return QD_OK;
+}
+
+// Host replay of the batched kernel over the encoded tables (debug).
+int qd_debug_batch_emulate(int32_t ncirc, const int32_t *nqudits, const int32_t *dims_concat, const qd_gate *gates,
+                           const int32_t *ngates, const int64_t *tune, double *amps, int64_t *info) {
+    if (ncirc < 1 || !nqudits || !dims_concat || !ngates || !amps || !info) return fail(QD_ERR_ARG, "bad arguments");
+    qd_batch b;
+    b.host_only = true;
+    if (int rc = batch_shape(&b, ncirc, nqudits, dims_concat)) return rc;
+    if (tune) {
+        const int32_t keys[4] = {QD_BATCH_TILE_AMPS, QD_BATCH_SMALL_AMPS, QD_BATCH_GROUP_AMPS, QD_BATCH_TILES_PER_ITEM};
+        for (int i = 0; i < 4; ++i)
+            if (tune[i] >= 0)
+                if (int rc = qd_batch_tune(&b, keys[i], tune[i])) return rc;
+    }
+    int g0 = 0;
+    for (int c = 0; c < ncirc; ++c) {
+        if (ngates[c] < 0) return fail(QD_ERR_ARG, "bad gate count");
+        if (int rc = batch_store(&b, c, gates ? gates + g0 : nullptr, ngates[c])) return rc;
+        g0 += ngates[c];
+    }
+    BatchTables tb;
+    if (int rc = batch_tables(&b, tb)) return rc;
+    std::vector<std::complex<double>> psi(b.total);
+    for (int c = 0; c < ncirc; ++c) psi[b.offs[c] + b.basis[c]] = 1.0;
+    std::vector<uint32_t> done(ncirc, 0);
+    std::vector<int> cur_seg(ncirc, -1);
+    std::vector<std::vector<uint32_t>> visits(ncirc);
+    int64_t errors = 0;
+    auto close_segment = [&](int c) {
+        for (uint32_t v : visits[c])
+            if (v != 1) errors |= 4;  // a segment's tiles must cover the register exactly once
+        std::fill(visits[c].begin(), visits[c].end(), 0u);
+    };
+    std::vector<std::complex<double>> st, v;
+    for (const BItem &it : tb.items) {
+        const int c = it.circuit;
+        const uint64_t N = b.N[c];
+        if (done[c] < it.wait_target) errors |= 1;  // would wait on a later item
+        if (visits[c].empty()) visits[c].assign(N, 0u);
+        if (cur_seg[c] != it.seg) {
+            if (cur_seg[c] >= 0) close_segment(c);
+            cur_seg[c] = it.seg;
+        }
+        const BSeg &S = tb.segs[it.seg];
+        st.assign(S.T, 0.0);
+        for (uint32_t t = it.first; t < it.first + it.count; ++t) {
+            if (t >= S.ntiles) {
+                errors |= 2;
+                continue;
+            }
+            const uint32_t base_t = expand(t, S.ex);
+            std::vector<uint64_t> idx(S.T);
+            for (uint32_t l = 0; l < S.T; ++l) {
+                const uint32_t h = fdiv(l, S.divB);
+                idx[l] = (uint64_t)base_t + (l - h * S.B) + tb.hoff[S.hoff + h];
+                if (idx[l] >= N) {
+                    errors |= 2;
+                    idx[l] = 0;
+                }
+                ++visits[c][idx[l]];
+                st[l] = psi[b.offs[c] + idx[l]];
+            }
+            for (int g = -1, ci = S.chunk0, gi = 0; ci < S.chunk0 + S.nchunks;) {
+                const BChunk &ch = tb.chunks[ci];
+                if (gi >= ch.ngates) {
+                    ++ci;
+                    gi = 0;
+                    continue;
+                }
+                if ((size_t)ch.ngates * sizeof(BGate) + (size_t)ch.ncoef * sizeof(float2) > kBatchDescBytes ||
+                    (ch.coef0 & 1u))
+                    errors |= 16;  // a chunk must fit its shared-memory area, 16-byte aligned
+                g = ch.gate0 + gi++;
+                const BGate &G = tb.gates[g];
+                if (G.coef + 2 * G.ncoef > ch.ncoef) errors |= 16;
+                auto cf = [&](int k, int n) {
+                    const float2 hi = tb.coef[ch.coef0 + G.coef + k], lo = tb.coef[ch.coef0 + G.coef + n + k];
+                    return std::complex<double>((double)hi.x + (double)lo.x, (double)hi.y + (double)lo.y);
+                };
+                v.assign(G.D, 0.0);
+                for (uint32_t r = 0; r < G.R; ++r) {
+                    const uint32_t base = expand(r, G.ex) + G.base;
+                    bool ok = true;
+                    for (int j = 0; j < G.D; ++j)
+                        if ((uint64_t)base + G.off[j] >= S.T) ok = false;
+                    if (!ok) {
+                        errors |= 8;
+                        continue;
+                    }
+                    for (int j = 0; j < G.D; ++j) v[j] = st[base + G.off[j]];
+                    for (int i = 0; i < G.D; ++i) {
+                        if (G.kind == 0) {
+                            std::complex<double> acc = 0.0;
+                            for (int j = 0; j < G.D; ++j) acc += cf(i * G.D + j, G.D * G.D) * v[j];
+                            st[base + G.off[i]] = acc;
+                        } else if ((G.active >> i) & 1u) {
+                            const std::complex<double> in = v[G.src[i]];
+                            st[base + G.off[i]] = ((G.unit >> i) & 1u) ? in : cf(i, G.D) * in;
+                        }
+                    }
+                }
+            }
+            for (uint32_t l = 0; l < S.T; ++l) psi[b.offs[c] + idx[l]] = st[l];
+        }
+        done[c] += it.count;
+    }
+    for (int c = 0; c < ncirc; ++c)
+        if (cur_seg[c] >= 0) close_segment(c);
+    for (uint64_t i = 0; i < b.total; ++i) {
+        amps[2 * i] = psi[i].real();
+        amps[2 * i + 1] = psi[i].imag();
+    }
+    info[0] = (int64_t)tb.segs.size();
+    info[1] = (int64_t)tb.items.size();
+    info[2] = (int64_t)tb.cap;
+    info[3] = (int64_t)tb.bytes;
+    info[4] = errors;
     return QD_OK;
 }
 

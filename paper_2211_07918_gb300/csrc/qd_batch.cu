@@ -3,29 +3,25 @@
 // persistent kernel launch, captured with the resets and the FP64
 // probability readout into one CUDA graph.
 //
-// Work items, dequeued in order from a global counter by persistent CTAs:
-//   * a small circuit (state fits in shared memory): one CTA loads the whole
-//     state, applies every gate of the circuit in shared memory and writes it
-//     back;
-//   * a large circuit: item (gate g, group range) applies gate g to a tile of
-//     its groups.  Before starting, the CTA waits until the circuit's
-//     completion counter shows every tile of gates < g done; after finishing
-//     it adds one to the counter.  Items are queued by gate level, so every
-//     item a CTA can wait on was dequeued earlier by a running CTA: the
-//     schedule cannot deadlock.  Waits are bounded (polls with __nanosleep);
-//     on expiry the CTA records an error in the device error word and skips
-//     the item.  State reads bypass L1 (ld.global.cg) so that a CTA never
-//     sees a stale copy of another CTA's writes.
-// Gates are encoded on the host (qd_batch_set_circuit) as dense D x D (FP32
-// hi + lo coefficient pairs, as in the per-gate kernels) or as permutations
-// with phases, D <= 25, with 32-bit index geometry (every register holds
-// fewer than 2^31 amplitudes).
+// Each circuit is cut into segments of consecutive gates whose acting qudits
+// fit one shared-memory tile (a circuit small enough is a single segment
+// whose one tile is the whole register).  A work item loads tiles of one
+// segment from the state into shared memory, applies every gate of the
+// segment there (one specialised loop per target dimension) and writes the
+// tiles back: one pass over the state per segment rather than per gate.
+//
+// Persistent CTAs dequeue items in order from a global counter.  An item of
+// segment k waits until the circuit's completion counter shows every tile of
+// segments < k done, and adds its tiles to the counter when finished.  Every
+// item waits only on items queued before it, and a CTA claims its next item
+// while it works on the current one (an item of lower index), so the
+// lowest-indexed unfinished item always belongs to a CTA whose dependencies
+// are complete: the schedule cannot deadlock.  Waits are bounded (polls with
+// __nanosleep); on expiry the CTA records an error in the device error word
+// and skips the item.  State reads bypass L1 (ld.global.cg) so that a CTA
+// never sees a stale copy of another CTA's writes.
 #include <algorithm>
-#include <cmath>
 #include <cstdint>
-#include <cstring>
-#include <string>
-#include <vector>
 
 #include <cuda_runtime.h>
 
@@ -38,10 +34,8 @@ namespace qd {
 
 namespace {
 
-constexpr int kBThreads = 256;
-constexpr uint32_t kPollLimit = 1u << 22;  // bounded waits on a circuit counter
-
-__device__ __forceinline__ float2 ldcg2(const float2 *p) { return __ldcg(p); }
+constexpr int kBThreads = 128;
+constexpr uint32_t kPollLimit = 1u << 22;  // bounded waits on a circuit counter (>= 0.5 s)
 
 __device__ __forceinline__ void cmac(float2 &acc, const float2 u, const float2 v) {
     acc.x = fmaf(u.x, v.x, acc.x);
@@ -50,125 +44,274 @@ __device__ __forceinline__ void cmac(float2 &acc, const float2 u, const float2 v
     acc.y = fmaf(u.y, v.x, acc.y);
 }
 
-// Load gate g's coefficients into shared memory (all threads).
-__device__ __forceinline__ void load_gate(const BGate &G, const float2 *__restrict__ coef, float2 *sU, float2 *sUlo) {
-    if (G.kind == 0) {
-        const int DD = G.D * G.D;
-        for (int i = threadIdx.x; i < DD; i += blockDim.x) {
-            sU[i] = coef[G.coef + i];
-            sUlo[i] = coef[G.coef + DD + i];
-        }
-    } else {
-        for (int i = threadIdx.x; i < G.D; i += blockDim.x) {
-            sU[i] = coef[G.coef + i];
-            sUlo[i] = coef[G.coef + G.D + i];
-        }
-    }
+// Copy a descriptor from global to shared memory (word by word, all threads).
+template <typename T>
+__device__ __forceinline__ void copy_desc(T *dst, const T *src) {
+    static_assert(sizeof(T) % 4 == 0, "descriptor size");
+    const uint32_t *s = reinterpret_cast<const uint32_t *>(src);
+    uint32_t *d = reinterpret_cast<uint32_t *>(dst);
+    for (int i = threadIdx.x; i < (int)(sizeof(T) / 4); i += blockDim.x) d[i] = __ldg(s + i);
 }
 
-// Apply gate G to group r of a state (global when SMEM == false).
-template <bool SMEM>
-__device__ __forceinline__ void apply_group(const BGate &G, float2 *psi, uint32_t r, const float2 *sU,
-                                            const float2 *sUlo) {
-    const uint32_t base = expand(r, G.ex) + G.base;
-    float2 v[kBatchMaxD];
-    if (G.kind == 0) {
+// Asynchronous 16-byte global -> shared copies (read-only tables only: the
+// copies may be served from L1).
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Issue the copies of one chunk: its gate descriptors, then its coefficients.
+__device__ __forceinline__ void load_chunk(const BChunk &ch, const BGate *__restrict__ gates,
+                                           const float2 *__restrict__ coef, unsigned char *desc) {
+    const uint4 *gsrc = reinterpret_cast<const uint4 *>(gates + ch.gate0);
+    uint4 *gdst = reinterpret_cast<uint4 *>(desc);
+    const int ng = ch.ngates * (int)(sizeof(BGate) / 16);
+    for (int i = threadIdx.x; i < ng; i += blockDim.x) cp_async16(gdst + i, gsrc + i);
+    const uint4 *csrc = reinterpret_cast<const uint4 *>(coef + ch.coef0);
+    uint4 *cdst = reinterpret_cast<uint4 *>(desc + ch.ngates * sizeof(BGate));
+    const int nc = (int)(ch.ncoef / 2);
+    for (int i = threadIdx.x; i < nc; i += blockDim.x) cp_async16(cdst + i, csrc + i);
+}
+
+// Dense gate of dimension D on the tile in shared memory; cf: hi block, then
+// lo block.  Each specialisation is its own function (called once per gate
+// and tile), so that the register demand of the large ones stays out of the
+// kernel body; above D = 10 the offsets are read from shared memory.
+template <int D>
+__device__ __noinline__ void dense_tile(const BGate &G, float2 *st, const float2 *cf) {
+    constexpr bool kRegOff = D <= 10;
+    uint32_t off[kRegOff ? D : 1];
+    if (kRegOff) {
 #pragma unroll
-        for (int j = 0; j < kBatchMaxD; ++j)
-            if (j < G.D) v[j] = SMEM ? psi[base + G.off[j]] : ldcg2(psi + base + G.off[j]);
-        for (int i = 0; i < G.D; ++i) {
+        for (int j = 0; j < D; ++j) off[kRegOff ? j : 0] = G.off[j];
+    }
+#define QD_OFF(j) (kRegOff ? off[kRegOff ? (j) : 0] : (uint32_t)G.off[j])
+    const float2 *hi = cf, *lo = cf + D * D;
+    for (uint32_t r = threadIdx.x; r < G.R; r += blockDim.x) {
+        const uint32_t base = expand(r, G.ex) + G.base;
+        float2 v[D];
+#pragma unroll
+        for (int j = 0; j < D; ++j) v[j] = st[base + QD_OFF(j)];
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
             float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int j = 0; j < kBatchMaxD; ++j)
-                if (j < G.D) cmac(acc, sUlo[i * G.D + j], v[j]);
+            for (int j = 0; j < D; ++j) cmac(acc, lo[i * D + j], v[j]);
 #pragma unroll
-            for (int j = 0; j < kBatchMaxD; ++j)
-                if (j < G.D) cmac(acc, sU[i * G.D + j], v[j]);
-            psi[base + G.off[i]] = acc;
+            for (int j = 0; j < D; ++j) cmac(acc, hi[i * D + j], v[j]);
+            st[base + QD_OFF(i)] = acc;
         }
-    } else {
+    }
+}
+
+// Permutation with phases of dimension D: out[i] = lam[i] in[src[i]] for the
+// active i (lam[i] == 1 exactly where unit bit i is set).
+template <int D>
+__device__ __noinline__ void mono_tile(const BGate &G, float2 *st, const float2 *cf) {
+    constexpr bool kRegOff = D <= 10;
+    uint32_t off[kRegOff ? D : 1], soff[kRegOff ? D : 1];  // soff[i] = off[src[i]]
+    if (kRegOff) {
 #pragma unroll
-        for (int i = 0; i < kBatchMaxD; ++i)
-            if (i < G.D && ((G.active >> i) & 1u))
-                v[i] = SMEM ? psi[base + G.off[G.src[i]]] : ldcg2(psi + base + G.off[G.src[i]]);
+        for (int j = 0; j < D; ++j) {
+            off[kRegOff ? j : 0] = G.off[j];
+            soff[kRegOff ? j : 0] = G.off[G.src[j]];
+        }
+    }
+#define QD_SOFF(i) (kRegOff ? soff[kRegOff ? (i) : 0] : (uint32_t)G.off[G.src[i]])
+    const float2 *hi = cf, *lo = cf + D;
+    const uint32_t active = G.active, unit = G.unit;
+    for (uint32_t r = threadIdx.x; r < G.R; r += blockDim.x) {
+        const uint32_t base = expand(r, G.ex) + G.base;
+        float2 v[D];
 #pragma unroll
-        for (int i = 0; i < kBatchMaxD; ++i) {
-            if (i < G.D && ((G.active >> i) & 1u)) {
+        for (int i = 0; i < D; ++i)
+            v[i] = ((active >> i) & 1u) ? st[base + QD_SOFF(i)] : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            if ((active >> i) & 1u) {
                 float2 o = v[i];
-                if (!((G.unit >> i) & 1u)) {
+                if (!((unit >> i) & 1u)) {
                     float2 acc = make_float2(0.f, 0.f);
-                    cmac(acc, sUlo[i], v[i]);
-                    cmac(acc, sU[i], v[i]);
+                    cmac(acc, lo[i], v[i]);
+                    cmac(acc, hi[i], v[i]);
                     o = acc;
                 }
-                psi[base + G.off[i]] = o;
+                st[base + QD_OFF(i)] = o;
+            }
+        }
+    }
+}
+#undef QD_OFF
+#undef QD_SOFF
+
+// Any D <= kBatchMaxD (dimensions that no specialisation covers).
+__device__ __noinline__ void generic_tile(const BGate &G, float2 *st, const float2 *cf) {
+    const int D = G.D;
+    const float2 *hi = cf, *lo = cf + G.ncoef;
+    for (uint32_t r = threadIdx.x; r < G.R; r += blockDim.x) {
+        const uint32_t base = expand(r, G.ex) + G.base;
+        float2 v[kBatchMaxD];
+        if (G.kind == 0) {
+            for (int j = 0; j < D; ++j) v[j] = st[base + G.off[j]];
+            for (int i = 0; i < D; ++i) {
+                float2 acc = make_float2(0.f, 0.f);
+                for (int j = 0; j < D; ++j) cmac(acc, lo[i * D + j], v[j]);
+                for (int j = 0; j < D; ++j) cmac(acc, hi[i * D + j], v[j]);
+                st[base + G.off[i]] = acc;
+            }
+        } else {
+            for (int i = 0; i < D; ++i)
+                if ((G.active >> i) & 1u) v[i] = st[base + G.off[G.src[i]]];
+            for (int i = 0; i < D; ++i) {
+                if ((G.active >> i) & 1u) {
+                    float2 o = v[i];
+                    if (!((G.unit >> i) & 1u)) {
+                        float2 acc = make_float2(0.f, 0.f);
+                        cmac(acc, lo[i], v[i]);
+                        cmac(acc, hi[i], v[i]);
+                        o = acc;
+                    }
+                    st[base + G.off[i]] = o;
+                }
             }
         }
     }
 }
 
-__global__ void __launch_bounds__(kBThreads) k_batch(float2 *__restrict__ arena, const uint64_t *__restrict__ offs,
-                                                     const uint32_t *__restrict__ sizes, const BGate *__restrict__ gates,
-                                                     const float2 *__restrict__ coef, const BItem *__restrict__ items,
-                                                     int32_t nitems, uint32_t *__restrict__ next,
-                                                     uint32_t *__restrict__ done, int32_t *__restrict__ err,
-                                                     uint32_t smem_amps) {
+__device__ __forceinline__ void apply_gate(const BGate &G, float2 *st, const float2 *cf) {
+#define QD_BATCH_CASE(DD)                         \
+    case DD:                                      \
+        if (G.kind == 0) dense_tile<DD>(G, st, cf); \
+        else mono_tile<DD>(G, st, cf);            \
+        break;
+    switch (G.D) {
+        QD_BATCH_CASE(2)
+        QD_BATCH_CASE(3)
+        QD_BATCH_CASE(4)
+        QD_BATCH_CASE(5)
+        QD_BATCH_CASE(6)
+        QD_BATCH_CASE(8)
+        QD_BATCH_CASE(9)
+        QD_BATCH_CASE(10)
+        QD_BATCH_CASE(12)
+        QD_BATCH_CASE(15)
+        QD_BATCH_CASE(16)
+        QD_BATCH_CASE(20)
+        QD_BATCH_CASE(25)
+        default:
+            generic_tile(G, st, cf);
+    }
+#undef QD_BATCH_CASE
+}
+
+// Gather (LOAD) or scatter one tile between the state and shared memory, 16
+// independent accesses in flight per thread.
+template <bool LOAD>
+__device__ __forceinline__ void move_tile(float2 *psi, float2 *st, const BSeg &S, uint32_t tb,
+                                          const uint32_t *__restrict__ hoff) {
+    constexpr int U = 16;
+    const uint32_t T = S.T, B = S.B;
+    const FastDiv32 divB = S.divB;
+    auto flat = [&](uint32_t l) {
+        const uint32_t h = fdiv(l, divB);
+        return tb + (l - h * B) + __ldg(hoff + h);
+    };
+    for (uint32_t l0 = threadIdx.x; l0 < T; l0 += U * kBThreads) {
+        if (LOAD) {
+            float2 v[U];
+#pragma unroll
+            for (int k = 0; k < U; ++k)
+                if (l0 + k * kBThreads < T) v[k] = __ldcg(psi + flat(l0 + k * kBThreads));
+#pragma unroll
+            for (int k = 0; k < U; ++k)
+                if (l0 + k * kBThreads < T) st[l0 + k * kBThreads] = v[k];
+        } else {
+#pragma unroll
+            for (int k = 0; k < U; ++k)
+                if (l0 + k * kBThreads < T) psi[flat(l0 + k * kBThreads)] = st[l0 + k * kBThreads];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kBThreads, 4)
+    k_batch(float2 *__restrict__ arena, const uint64_t *__restrict__ offs, const BSeg *__restrict__ segs,
+            const BChunk *__restrict__ chunks, const BGate *__restrict__ gates, const float2 *__restrict__ coef,
+            const uint32_t *__restrict__ hofftab, const BItem *__restrict__ items, int32_t nitems,
+            uint32_t *__restrict__ next, uint32_t *__restrict__ done, int32_t *__restrict__ err) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    float2 *sU = reinterpret_cast<float2 *>(smraw);
-    float2 *sUlo = sU + kBatchMaxD * kBatchMaxD;
-    float2 *sstate = sUlo + kBatchMaxD * kBatchMaxD;
-    __shared__ int32_t item_id;
-    __shared__ int32_t ok;
+    BSeg &S = *reinterpret_cast<BSeg *>(smraw);
+    unsigned char *desc = smraw + ((sizeof(BSeg) + 15) / 16) * 16;
+    float2 *st = reinterpret_cast<float2 *>(desc + kBatchDescBytes);
+    __shared__ BChunk s_ch;
+    __shared__ int32_t s_item;
+    __shared__ int32_t s_ok;
+    int32_t nxt = 0;
+    if (threadIdx.x == 0) nxt = (int32_t)atomicAdd(next, 1u);
     for (;;) {
-        if (threadIdx.x == 0) item_id = (int32_t)atomicAdd(next, 1u);
+        if (threadIdx.x == 0) s_item = nxt;
         __syncthreads();
-        const int32_t id = item_id;
+        const int32_t id = s_item;
         if (id >= nitems) break;
         const BItem it = items[id];
-        float2 *psi = arena + offs[it.circuit];
-        if (it.ngates > 0) {
-            // ---- small circuit in shared memory
-            const uint32_t N = sizes[it.circuit];
-            for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) sstate[i] = ldcg2(psi + i);
-            for (int g = it.gate; g < it.gate + it.ngates; ++g) {
-                const BGate &G = gates[g];
-                __syncthreads();
-                load_gate(G, coef, sU, sUlo);
-                __syncthreads();
-                for (uint32_t r = threadIdx.x; r < G.R; r += blockDim.x) apply_group<true>(G, sstate, r, sU, sUlo);
-            }
-            __syncthreads();
-            for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) psi[i] = sstate[i];
-            __syncthreads();
-            continue;
-        }
-        // ---- tile of a large circuit's gate: wait for the earlier gates
         if (threadIdx.x == 0) {
-            ok = 1;
+            nxt = (int32_t)atomicAdd(next, 1u);  // claim the following item now
+            s_ok = 1;
             const volatile uint32_t *d = done + it.circuit;
             uint32_t polls = 0;
             while (*d < it.wait_target) {
                 if (++polls > kPollLimit) {
                     atomicExch(err, 2);
-                    ok = 0;
+                    s_ok = 0;
                     break;
                 }
                 __nanosleep(128);
             }
             __threadfence();
         }
+        copy_desc(&S, segs + it.seg);
         __syncthreads();
-        if (ok) {
-            const BGate &G = gates[it.gate];
-            load_gate(G, coef, sU, sUlo);
-            __syncthreads();
-            for (uint32_t r = it.first + threadIdx.x; r < it.first + it.count; r += blockDim.x)
-                apply_group<false>(G, psi, r, sU, sUlo);
+        if (s_ok) {
+            float2 *psi = arena + offs[it.circuit];
+            const uint32_t *hoff = hofftab + S.hoff;
+            const bool one_chunk = S.nchunks == 1;
+            for (uint32_t t = it.first; t < it.first + it.count; ++t) {
+                const uint32_t tb = expand(t, S.ex);
+                for (int c = 0; c < S.nchunks; ++c) {
+                    const bool fresh = !(one_chunk && t > it.first);
+                    if (fresh) {
+                        if (threadIdx.x == 0) s_ch = chunks[S.chunk0 + c];
+                        __syncthreads();
+                        load_chunk(s_ch, gates, coef, desc);
+                    }
+                    if (c == 0) move_tile<true>(psi, st, S, tb, hoff);
+                    if (fresh) cp_async_wait_all();
+                    __syncthreads();
+                    // s_ch is read once here, before the first gate's barrier: thread 0
+                    // rewrites it for the next chunk after the last gate's barrier
+                    const int ng = s_ch.ngates;
+                    const BGate *sg = reinterpret_cast<const BGate *>(desc);
+                    const float2 *sc = reinterpret_cast<const float2 *>(desc + ng * sizeof(BGate));
+                    for (int g = 0; g < ng; ++g) {
+                        const BGate &G = sg[g];
+                        // descriptor sanity: a gate's groups stay inside the tile and its
+                        // coefficients inside the chunk (else: error word, gate skipped)
+                        if (G.D >= 2 && G.D <= kBatchMaxD && (uint64_t)G.R * (uint32_t)G.D <= S.T &&
+                            ng * sizeof(BGate) + (size_t)(G.coef + 2 * G.ncoef) * sizeof(float2) <= kBatchDescBytes)
+                            apply_gate(G, st, sc + G.coef);
+                        else if (threadIdx.x == 0)
+                            atomicExch(err, 3);
+                        __syncthreads();
+                    }
+                }
+                move_tile<false>(psi, st, S, tb, hoff);
+                __syncthreads();
+            }
         }
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence();
-            atomicAdd(done + it.circuit, 1u);
+            atomicAdd(done + it.circuit, it.count);
         }
     }
 }
@@ -187,8 +330,23 @@ __global__ void k_batch_ones(float2 *arena, const uint64_t *offs, const uint64_t
 
 }  // namespace
 
-size_t batch_smem_bytes(uint32_t smem_amps) {
-    return (size_t)2 * kBatchMaxD * kBatchMaxD * sizeof(float2) + (size_t)smem_amps * sizeof(float2);
+size_t batch_smem_bytes(uint32_t tile_cap) {
+    return ((sizeof(BSeg) + 15) / 16) * 16 + kBatchDescBytes + (size_t)tile_cap * sizeof(float2);
+}
+
+int batch_occupancy(uint32_t tile_cap) {
+    const size_t smem = batch_smem_bytes(tile_cap);
+    if (cudaFuncSetAttribute((const void *)k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch, kBThreads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return occ;
 }
 
 cudaError_t batch_launch(const BatchLaunch &b, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1) {
@@ -196,21 +354,21 @@ cudaError_t batch_launch(const BatchLaunch &b, cudaStream_t s, cudaEvent_t ev0, 
     if (e != cudaSuccess) return e;
     k_batch_init<<<b.sm_count * 4, 256, 0, s>>>(b.arena, b.total);
     k_batch_ones<<<(b.ncirc + 255) / 256, 256, 0, s>>>(b.arena, b.offs, b.basis, b.ncirc);
-    const size_t smem = batch_smem_bytes(b.smem_amps);
-    e = cudaFuncSetAttribute((const void *)k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    if (b.nitems == 0) return probabilities(b.arena, 1, b.total, b.probs, b.sm_count, s);
-    int occ = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch, kBThreads, smem);
-    if (occ < 1) occ = 1;
-    const int per_sm = b.ctas_per_sm > 0 && b.ctas_per_sm < occ ? b.ctas_per_sm : occ;
-    const int grid = b.sm_count * per_sm;
-    if (ev0) cudaEventRecord(ev0, s);
-    k_batch<<<grid, kBThreads, smem, s>>>(b.arena, b.offs, b.sizes, b.gates, b.coef, b.items, b.nitems, b.counters,
-                                         b.counters + 1, b.err, b.smem_amps);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    if (ev1) cudaEventRecord(ev1, s);
+    if (b.nitems > 0) {
+        const size_t smem = batch_smem_bytes(b.tile_cap);
+        const int occ = std::max(1, batch_occupancy(b.tile_cap));
+        const int per_sm = b.ctas_per_sm > 0 && b.ctas_per_sm < occ ? b.ctas_per_sm : occ;
+        const int grid = b.sm_count * per_sm;
+        if (ev0) cudaEventRecord(ev0, s);
+        k_batch<<<grid, kBThreads, smem, s>>>(b.arena, b.offs, b.segs, b.chunks, b.gates, b.coef, b.hoff, b.items,
+                                             b.nitems, b.counters, b.counters + 1, b.err);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        if (ev1) cudaEventRecord(ev1, s);
+    } else if (ev0) {
+        cudaEventRecord(ev0, s);
+        cudaEventRecord(ev1, s);
+    }
     return probabilities(b.arena, 1, b.total, b.probs, b.sm_count, s);
 }
 

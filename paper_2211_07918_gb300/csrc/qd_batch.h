@@ -1,5 +1,5 @@
-// Batched persistent execution (qd_batch.cu): device-side gate encoding and
-// launch description shared with the host API in qd_api.cu.
+// Batched persistent execution (qd_batch.cu): device-side encoding of
+// segments, gates and work items, shared with the host API in qd_api.cu.
 #pragma once
 #include <cstddef>
 #include <cstdint>
@@ -9,31 +9,82 @@
 
 namespace qd {
 
-constexpr int kBatchMaxD = 25;  // largest target dimension of a batched gate
+constexpr int kBatchMaxD = 25;          // largest target dimension of a batched gate
+constexpr uint32_t kBatchMaxTile = 24576;  // largest tile (amplitudes) kept in shared memory
 
-// One gate of a batched circuit, 32-bit geometry (direct mode): dense
-// (kind 0, D x D coefficients at coef: hi block then lo block) or a
-// permutation with phases (kind 1, D phases at coef: hi then lo).
-struct BGate {
-    int32_t kind;
-    int32_t D;
-    uint32_t R;     // groups
-    uint32_t base;  // control offset
-    Expand32 ex;
-    uint32_t off[kBatchMaxD];
-    int32_t src[kBatchMaxD];
-    uint32_t active, unit;
-    uint64_t coef;  // offset (float2 units) into the coefficient arena
+constexpr int kBExMax = 8;              // insertion runs of a tile-local gate (<= 14 local qudits)
+constexpr uint32_t kBatchDescBytes = 16384;  // shared memory for one chunk of gate descriptors + coefficients
+
+// Insert-digit expansion with at most kBExMax runs (adjacent removed qudits
+// merged into one run).
+struct BEx {
+    int32_t n;
+    int32_t pad;
+    FastDiv32 div[kBExMax];
+    uint32_t span[kBExMax];
 };
 
-// One work item: a whole small circuit (ngates > 0) or a tile of one gate of
-// a large circuit (ngates == 0) that waits for wait_target completed tiles.
+__host__ __device__ __forceinline__ uint32_t expand(uint32_t r, const BEx &e) {
+#pragma unroll
+    for (int k = 0; k < kBExMax; ++k) {
+        if (k < e.n) {
+            const uint32_t q = fdiv(r, e.div[k]);
+            const uint32_t lo = r - q * e.div[k].d;
+            r = q * e.span[k] + lo;
+        }
+    }
+    return r;
+}
+
+// One gate in the local index space of its segment's tile (32-bit direct
+// geometry): dense (kind 0, D x D coefficients) or a permutation with phases
+// (kind 1, D phases).  Coefficients: ncoef FP32 "hi" entries at coef (float2
+// offset inside its chunk's coefficient block), then ncoef "lo" entries.
+struct __align__(16) BGate {
+    int32_t kind;
+    int32_t D;
+    uint32_t R;     // groups in the tile
+    uint32_t base;  // control offset in the tile
+    uint32_t active, unit;
+    uint32_t coef;
+    uint32_t ncoef;
+    BEx ex;         // group index -> tile-local base
+    uint16_t off[kBatchMaxD];
+    int8_t src[kBatchMaxD];
+};
+
+// Consecutive gates of a segment whose descriptors and coefficients fit
+// kBatchDescBytes of shared memory, loaded together.
+struct BChunk {
+    int32_t gate0, ngates;
+    uint32_t coef0;  // float2 offset of the coefficient block (even: 16-byte aligned)
+    uint32_t ncoef;  // float2 entries of the block
+};
+
+// A segment: consecutive gates of one circuit whose acting qudits all lie in
+// a qudit set S.  The register splits into N / T tiles of T = prod_{q in S} d_q
+// amplitudes (one tile per assignment of the other qudits).  Tile-local index
+// l = j + B h, where j < B runs over the qudits below the lowest qudit missing
+// from S (contiguous in the register) and h over the rest of S; the flat
+// index is expand(tile, ex) + j + hoff[h].
+struct BSeg {
+    int32_t chunk0, nchunks;
+    uint32_t T, B;
+    FastDiv32 divB;
+    uint32_t hoff;          // offset of this segment's run table in the run-table arena
+    uint32_t ntiles;
+    Expand32 ex;            // tile index -> flat base of the tile
+};
+
+// One work item: tiles [first, first + count) of segment seg of a circuit,
+// started once the circuit's completion counter reaches wait_target (every
+// tile of the circuit's earlier segments is done).
 struct BItem {
     int32_t circuit;
-    int32_t gate;
-    int32_t ngates;
+    int32_t seg;
     uint32_t first, count;
     uint32_t wait_target;
+    uint32_t pad;
 };
 
 struct BatchLaunch {
@@ -41,9 +92,11 @@ struct BatchLaunch {
     uint64_t total;
     const uint64_t *offs;
     const uint64_t *basis;
-    const uint32_t *sizes;
+    const BSeg *segs;
+    const BChunk *chunks;
     const BGate *gates;
     const float2 *coef;
+    const uint32_t *hoff;
     const BItem *items;
     int32_t nitems;
     int32_t ncirc;
@@ -52,13 +105,15 @@ struct BatchLaunch {
     double *probs;
     int sm_count;
     int ctas_per_sm;     // 0: as many as fit
-    uint32_t smem_amps;  // largest state kept whole in shared memory
+    uint32_t tile_cap;   // largest tile of any segment (shared-memory amplitudes)
 };
 
-size_t batch_smem_bytes(uint32_t smem_amps);
-// Enqueue: reset the counters and every state to |0...0>, the persistent
-// kernel, and the FP64 probabilities of the whole arena.
-// When ev0/ev1 are given they are recorded around the persistent kernel.
+size_t batch_smem_bytes(uint32_t tile_cap);
+// Enqueue: reset the counters and every state to its basis state, the
+// persistent kernel, and the FP64 probabilities of the whole arena.  When
+// ev0/ev1 are given they are recorded around the persistent kernel.
 cudaError_t batch_launch(const BatchLaunch &b, cudaStream_t s, cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr);
+// Resident CTAs per SM of the persistent kernel for a tile capacity.
+int batch_occupancy(uint32_t tile_cap);
 
 }  // namespace qd

@@ -25,6 +25,7 @@ QD_MAX_TARGETS, QD_MAX_CONTROLS = 6, 8
 QD_TUNE_TILE_STRIDE, QD_TUNE_FUSE_KMAX, QD_TUNE_FUSE_DMAX = 1, 2, 3
 QD_MODEL_FEATURES, QD_MODEL_PARAMS = 12, 9217
 QD_BATCH_TILE_AMPS, QD_BATCH_CTAS_PER_SM, QD_BATCH_SMALL_AMPS, QD_BATCH_GROUP_AMPS = 1, 2, 3, 4
+QD_BATCH_TILES_PER_ITEM = 5
 ERRORS = {-1: "QD_ERR_ARG", -2: "QD_ERR_DIM", -3: "QD_ERR_OVERLAP", -4: "QD_ERR_OOM", -5: "QD_ERR_CUDA",
           -6: "QD_ERR_TIMEOUT", -7: "QD_ERR_DEVICE", -8: "QD_ERR_UNSUPPORTED"}
 
@@ -474,6 +475,34 @@ def qd_debug_gate_members(dims: Sequence[int], gate, cap: int = 1 << 20, tile_st
 
 def qd_debug_gate_members_tuned(dims: Sequence[int], gate, tile_stride: int, cap: int = 1 << 20):
     return qd_debug_gate_members(dims, gate, cap, tile_stride)
+
+
+def qd_debug_batch_emulate(circuits, tile_amps: int = -1, small_amps: int = -1, group_amps: int = -1,
+                           tiles_per_item: int = -1):
+    """Host replay of a batched run (see include/qudit_debug.h): returns the
+    final FP64 states (one array per circuit) and the info dict."""
+    L = load()
+    fn = L.qd_debug_batch_emulate
+    fn.argtypes = [_i32, _i32p, _i32p, ctypes.POINTER(QdGate), _i32p, _i64p, _dp, _i64p]
+    fn.restype = ctypes.c_int
+    nq, nqp = _arr_i32([len(d) for d, _ in circuits])
+    dc, dcp = _arr_i32([int(x) for d, _ in circuits for x in d])
+    ng, ngp = _arr_i32([len(g) for _, g in circuits])
+    allg = [g for _, gs in circuits for g in gs]
+    ga = GateArray(allg)
+    tune = np.array([tile_amps, small_amps, group_amps, tiles_per_item], dtype=np.int64)
+    Ns = [int(np.prod(d)) for d, _ in circuits]
+    amps = np.zeros(2 * sum(Ns), dtype=np.float64)
+    info = np.zeros(5, dtype=np.int64)
+    _check(fn(len(circuits), nqp, dcp, ga.ptr if allg else None, ngp, tune.ctypes.data_as(_i64p),
+              amps.ctypes.data_as(_dp), info.ctypes.data_as(_i64p)))
+    z = amps.view(np.complex128)
+    out, o = [], 0
+    for n in Ns:
+        out.append(z[o:o + n].copy())
+        o += n
+    keys = ["segments", "items", "max_tile", "alg_bytes", "errors"]
+    return out, {k: int(v) for k, v in zip(keys, info)}
 
 
 def qd_debug_fuse_plan(dims, gates, plan_kind, precision=QD_C64, kmax=3, dmax=32):

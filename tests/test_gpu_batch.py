@@ -71,21 +71,34 @@ def check_circuit(dims, gates, psi, p):
 
 
 # Register sizes span 4 .. 5^7 = 78,125 amplitudes: with the default limit of
-# 6,144 amplitudes in shared memory, both the whole-circuit items and the
-# tiled gate items run.
+# 6,144 amplitudes in shared memory, both whole-register items and tiled
+# segments run.
 @pytest.mark.parametrize("tune", [
     (),
     ((L.QD_BATCH_SMALL_AMPS, 0),),                                  # every circuit tiled
-    ((L.QD_BATCH_SMALL_AMPS, 0), (L.QD_BATCH_TILE_AMPS, 100)),      # many ragged tiles
-    ((L.QD_BATCH_SMALL_AMPS, 24576), (L.QD_BATCH_CTAS_PER_SM, 1)),  # mostly in shared memory
-    ((L.QD_BATCH_TILE_AMPS, 1 << 20), (L.QD_BATCH_CTAS_PER_SM, 3)),  # one tile per gate
-], ids=["default", "all_tiled", "ragged_tiles", "smem_1cta", "one_tile"])
+    ((L.QD_BATCH_SMALL_AMPS, 0), (L.QD_BATCH_TILE_AMPS, 100)),      # small tiles, one gate each
+    ((L.QD_BATCH_SMALL_AMPS, 24576), (L.QD_BATCH_CTAS_PER_SM, 1)),  # mostly whole registers
+    ((L.QD_BATCH_TILE_AMPS, 24576), (L.QD_BATCH_CTAS_PER_SM, 3)),   # largest tiles
+    ((L.QD_BATCH_SMALL_AMPS, 0), (L.QD_BATCH_TILE_AMPS, 600), (L.QD_BATCH_TILES_PER_ITEM, 3),
+     (L.QD_BATCH_GROUP_AMPS, 1)),                                    # several tiles per item, no groups
+], ids=["default", "all_tiled", "tile100", "smem_1cta", "big_tiles", "multi_tile_items"])
 def test_batch_vs_oracle(tune):
     circuits = mixed_batch(9100, 24, 40)
     amps, probs, info = run_batch(circuits, tune)
     assert info["device_error"] == 0
     for (d, g), psi, p in zip(circuits, amps, probs):
         check_circuit(d, g, psi, p)
+
+
+def test_batch_long_circuits_many_chunks():
+    # 300 gates on whole-register segments: each segment's descriptors span
+    # several shared-memory chunks, loaded one after another
+    circuits = mixed_batch(9300, 16, 300, nmin=3, nmax=6)
+    for tune in ((), ((L.QD_BATCH_SMALL_AMPS, 0), (L.QD_BATCH_TILE_AMPS, 512), (L.QD_BATCH_TILES_PER_ITEM, 2))):
+        amps, probs, info = run_batch(circuits, tune)
+        assert info["device_error"] == 0
+        for (d, g), psi, p in zip(circuits, amps, probs):
+            check_circuit(d, g, psi, p)
 
 
 def test_batch_graph_replay_on_stream():
@@ -131,18 +144,23 @@ def test_batch_rejections():
     assert e.value.code == -2
     with pytest.raises(L.QuditError):
         L.qd_batch_create([[3, 1]])
-    b = L.qd_batch_create([[6, 6], [2, 2]])
+    b = L.qd_batch_create([[6, 6], [2, 2], [64, 64, 8]])
     try:
         rng = np.random.default_rng(5)
         with pytest.raises(L.QuditError) as e:  # D = 36 > 25
             L.qd_batch_set_circuit(b, 0, [Gate("U", (0, 1), matrix=wl.haar_unitary(36, rng))])
         assert e.value.code == -2
+        with pytest.raises(L.QuditError) as e:  # acting qudits span 32768 amplitudes
+            L.qd_batch_set_circuit(b, 2, [Gate("X", (2,), (0, 1), (1, 1), 1)])
+        assert e.value.code == -8
         with pytest.raises(L.QuditError):
-            L.qd_batch_set_circuit(b, 2, [])
+            L.qd_batch_set_circuit(b, 3, [])
         with pytest.raises(L.QuditError):
             L.qd_batch_set_circuit(b, 1, [Gate("X", (0,), (0,), (1,), 1)])  # control == target
         with pytest.raises(L.QuditError):
             L.qd_batch_tune(b, 99, 1)
+        with pytest.raises(L.QuditError):
+            L.qd_batch_tune(b, L.QD_BATCH_TILE_AMPS, 1 << 20)
     finally:
         L.qd_batch_destroy(b)
 
