@@ -381,6 +381,7 @@ def run_c3(args, rank, world, local):
     b = L.qd_batch_create(regs, stream.cuda_stream)
     for c, (_, g) in enumerate(circuits):
         L.qd_batch_set_circuit(b, c, g)
+    tuned = L.qd_batch_autotune(b, 1)  # launch shape, chosen before the timed region
 
     def timed(run, steps, warmup):
         for _ in range(warmup):
@@ -469,7 +470,7 @@ def run_c3(args, rank, world, local):
                    "states (1.95 GB) larger than L2",
                    "step": "reset all registers + all circuits + FP64 probabilities of every register"},
         "amp_updates_per_s": world * amp_updates / (ms_step * 1e-3),
-        "batch": {"items": info["items"], "device_error": max(info["device_error"], err),
+        "batch": {"items": info["items"], "device_error": max(info["device_error"], err), "autotuned": tuned,
                   "prob_sums_sampled": sums, "kernel_ms": kmean, "kernel_share": kmean / ms_step},
         "compare": {"per_circuit_plans_ms_per_step": float(np.mean(ms_per)),
                     "per_circuit_plans_gates_per_s": world * ngates / (float(np.mean(ms_per)) * 1e-3),

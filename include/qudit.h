@@ -275,10 +275,10 @@ int qd_sync(qd_reg *reg, int32_t *device_error);
 typedef struct qd_batch qd_batch;
 #define QD_BATCH_TILE_AMPS 1   /* largest shared-memory tile of a large circuit's segment (default 4096) */
 #define QD_BATCH_CTAS_PER_SM 2 /* persistent CTAs per SM (0: as many as fit; default 0) */
-#define QD_BATCH_SMALL_AMPS 3  /* largest register simulated whole in shared memory (default 6144) */
+#define QD_BATCH_SMALL_AMPS 3  /* largest register simulated whole in shared memory (default 2048) */
 #define QD_BATCH_GROUP_AMPS 4  /* large circuits are queued in groups of about this many amplitudes,
                                   level by level within a group, so that a group's states stay in L2
-                                  (default 2^23) */
+                                  (default 2^25) */
 #define QD_BATCH_TILES_PER_ITEM 5 /* tiles one work item processes (default 1) */
 /* ncirc registers; register c has nqudits[c] qudits whose dims follow in
  * dims_concat (concatenated in circuit order).  stream: cudaStream_t as void*. */
@@ -306,6 +306,13 @@ int qd_batch_info(qd_batch *b, int64_t *total_amplitudes, int32_t *items, int32_
  * writes its register once: 16 bytes per complex64 amplitude per segment). */
 int qd_batch_profile(qd_batch *b, int32_t enable);
 int qd_batch_timings(qd_batch *b, float *kernel_ms, double *alg_bytes);
+/* Autotuner: runs the batch (reps timed runs after one warm-up run each) in
+ * a fixed set of launch shapes - tile amplitudes, shared-memory register
+ * limit, CTAs per SM, tiles per item - and keeps the one whose persistent
+ * kernel was fastest.  chosen (4 int64, may be NULL): tile amplitudes, small
+ * register limit, CTAs per SM, tiles per item; best_ms (may be NULL): its
+ * kernel time.  Synchronises; the registers hold the last run's result. */
+int qd_batch_autotune(qd_batch *b, int32_t reps, int64_t *chosen, float *best_ms);
 int qd_batch_destroy(qd_batch *b);
 
 /* ---- learned cost model ------------------------------------------------ */

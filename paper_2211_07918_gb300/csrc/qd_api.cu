@@ -1478,10 +1478,11 @@ struct qd_batch {
     uint64_t total = 0;
     uint32_t tile_amps = 4096;
     int32_t ctas_per_sm = 0;
-    uint32_t small_amps = 6144;
-    uint64_t group_amps = uint64_t(1) << 23;
+    uint32_t small_amps = 2048;
+    uint64_t group_amps = uint64_t(1) << 25;
     uint32_t tiles_per_item = 1;
     uint32_t tile_cap = 0;
+    uint32_t desc_bytes = kBatchDescBytes;
     double alg_bytes = 0;
     int64_t nsegs = 0;
     bool profile = false;
@@ -1573,7 +1574,7 @@ std::vector<std::pair<int, uint64_t>> batch_segments(const qd_batch *b, int c, u
     return segs;
 }
 
-// FP32 hi + lo pairs of a gate's coefficients (dense: D x D, else D phases),
+// FP32 hi + lo parts of a gate's coefficients (dense: D x D, else D phases),
 // appended to coef: ncoef hi entries, then ncoef lo entries.
 void split_coef(const GatePlan &g, BGate &bg, std::vector<float2> &coef) {
     const int n = bg.kind == 0 ? g.D * g.D : g.D;
@@ -1620,6 +1621,7 @@ struct BatchTables {
     std::vector<uint32_t> hoff;
     std::vector<BItem> items;
     uint32_t cap = 1;
+    uint32_t desc_bytes = kBatchDescBytes;  // largest chunk, at least the target size
     double bytes = 0;
 };
 
@@ -1778,6 +1780,11 @@ int batch_tables(const qd_batch *b, BatchTables &tb) {
     if (!grp.empty()) flush_group();
     tb.cap = std::max<uint32_t>(cap, 1);
     tb.bytes = bytes;
+    tb.desc_bytes = kBatchDescBytes;
+    for (const BChunk &ch : chunks) {
+        const size_t need = (size_t)ch.ngates * sizeof(BGate) + (size_t)ch.ncoef * sizeof(float2);
+        tb.desc_bytes = std::max<uint32_t>(tb.desc_bytes, (uint32_t)((need + 15) / 16 * 16));
+    }
     return QD_OK;
 }
 
@@ -1795,6 +1802,7 @@ int batch_prepare(qd_batch *b) {
     b->nsegs = (int64_t)segs.size();
     b->alg_bytes = tb.bytes;
     b->tile_cap = tb.cap;
+    b->desc_bytes = tb.desc_bytes;
     auto up = [&](void **dst, const void *src, size_t bytes_) -> int {
         if (bytes_ == 0) bytes_ = 16;
         if (cudaMalloc(dst, bytes_) != cudaSuccess) {
@@ -1891,6 +1899,7 @@ BatchLaunch batch_desc(const qd_batch *b) {
     L.sm_count = b->sm_count;
     L.ctas_per_sm = b->ctas_per_sm;
     L.tile_cap = b->tile_cap;
+    L.desc_bytes = b->desc_bytes;
     return L;
 }
 
@@ -1990,7 +1999,7 @@ int qd_batch_run(qd_batch *b) {
         return QD_OK;
     }
     if (!b->exec) {
-        batch_occupancy(b->tile_cap);  // sets the kernel's shared-memory attribute outside the capture
+        batch_occupancy(b->tile_cap, b->desc_bytes);  // sets the kernel's shared-memory attribute outside the capture
         QD_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
         cudaError_t e = batch_launch(desc, b->stream);
         cudaGraph_t graph = nullptr;
@@ -2063,6 +2072,59 @@ int qd_batch_timings(qd_batch *b, float *kernel_ms, double *alg_bytes) {
         QD_CUDA(cudaEventSynchronize(b->ev1));
         QD_CUDA(cudaEventElapsedTime(kernel_ms, b->ev0, b->ev1));
     }
+    return QD_OK;
+}
+
+int qd_batch_autotune(qd_batch *b, int32_t reps, int64_t *chosen, float *best_ms) {
+    if (!b || reps < 1) return fail(QD_ERR_ARG, "bad arguments");
+    struct Shape {
+        uint32_t tile, small;
+        int32_t ctas;
+        uint32_t tpi;
+    };
+    const Shape cand[] = {{4096, 2048, 0, 1}, {2048, 2048, 0, 1}, {8192, 2048, 0, 1}, {4096, 1024, 0, 1},
+                          {4096, 6144, 0, 1}, {4096, 2048, 4, 1}, {4096, 2048, 0, 2}, {6144, 2048, 0, 1}};
+    const bool was_profile = b->profile;
+    b->profile = true;
+    float best = 0.f;
+    int bi = -1;
+    for (int i = 0; i < (int)(sizeof(cand) / sizeof(cand[0])); ++i) {
+        b->tile_amps = cand[i].tile;
+        b->small_amps = cand[i].small;
+        b->ctas_per_sm = cand[i].ctas;
+        b->tiles_per_item = cand[i].tpi;
+        b->dirty = true;
+        float t = 0.f;
+        for (int k = 0; k <= reps; ++k) {  // the first run prepares and warms up
+            if (int rc = qd_batch_run(b)) {
+                b->profile = was_profile;
+                return rc;
+            }
+            float ms = 0.f;
+            if (int rc = qd_batch_timings(b, &ms, nullptr)) {
+                b->profile = was_profile;
+                return rc;
+            }
+            if (k > 0) t = (k == 1) ? ms : std::min(t, ms);
+        }
+        if (bi < 0 || t < best) {
+            best = t;
+            bi = i;
+        }
+    }
+    b->profile = was_profile;
+    b->tile_amps = cand[bi].tile;
+    b->small_amps = cand[bi].small;
+    b->ctas_per_sm = cand[bi].ctas;
+    b->tiles_per_item = cand[bi].tpi;
+    b->dirty = true;
+    if (chosen) {
+        chosen[0] = cand[bi].tile;
+        chosen[1] = cand[bi].small;
+        chosen[2] = cand[bi].ctas;
+        chosen[3] = cand[bi].tpi;
+    }
+    if (best_ms) *best_ms = best;
     return QD_OK;
 }
 
@@ -2139,12 +2201,12 @@ int qd_debug_batch_emulate(int32_t ncirc, const int32_t *nqudits, const int32_t 
                     gi = 0;
                     continue;
                 }
-                if ((size_t)ch.ngates * sizeof(BGate) + (size_t)ch.ncoef * sizeof(float2) > kBatchDescBytes ||
-                    (ch.coef0 & 1u))
+                if ((size_t)ch.ngates * sizeof(BGate) + (size_t)ch.ncoef * sizeof(float2) > tb.desc_bytes ||
+                    (ch.coef0 & 1u) || (tb.desc_bytes & 15u))
                     errors |= 16;  // a chunk must fit its shared-memory area, 16-byte aligned
                 g = ch.gate0 + gi++;
                 const BGate &G = tb.gates[g];
-                if (G.coef + 2 * G.ncoef > ch.ncoef) errors |= 16;
+                if (G.coef + 2 * G.ncoef > ch.ncoef || (G.coef & 1u)) errors |= 16;
                 auto cf = [&](int k, int n) {
                     const float2 hi = tb.coef[ch.coef0 + G.coef + k], lo = tb.coef[ch.coef0 + G.coef + n + k];
                     return std::complex<double>((double)hi.x + (double)lo.x, (double)hi.y + (double)lo.y);

@@ -37,13 +37,6 @@ namespace {
 constexpr int kBThreads = 128;
 constexpr uint32_t kPollLimit = 1u << 22;  // bounded waits on a circuit counter (>= 0.5 s)
 
-__device__ __forceinline__ void cmac(float2 &acc, const float2 u, const float2 v) {
-    acc.x = fmaf(u.x, v.x, acc.x);
-    acc.x = fmaf(-u.y, v.y, acc.x);
-    acc.y = fmaf(u.x, v.y, acc.y);
-    acc.y = fmaf(u.y, v.x, acc.y);
-}
-
 // Copy a descriptor from global to shared memory (word by word, all threads).
 template <typename T>
 __device__ __forceinline__ void copy_desc(T *dst, const T *src) {
@@ -74,70 +67,192 @@ __device__ __forceinline__ void load_chunk(const BChunk &ch, const BGate *__rest
     for (int i = threadIdx.x; i < nc; i += blockDim.x) cp_async16(cdst + i, csrc + i);
 }
 
-// Dense gate of dimension D on the tile in shared memory; cf: hi block, then
-// lo block.  Each specialisation is its own function (called once per gate
-// and tile), so that the register demand of the large ones stays out of the
-// kernel body; above D = 10 the offsets are read from shared memory.
+// Packed FP32 pairs (Blackwell fma.rn.f32x2: two FMAs, each rounded as fmaf).
+typedef unsigned long long f2p;
+
+__device__ __forceinline__ f2p pack2(float a, float b) {
+    f2p r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float2 unpack2(f2p r) {
+    float a, b;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+    return make_float2(a, b);
+}
+__device__ __forceinline__ f2p fma2(f2p a, f2p b, f2p c) {
+    f2p d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+// Coefficients u = hi + lo (FP32 each) are stored as a hi block then a lo
+// block.  A dot product sum_j u_j v_j takes every lo term first and then
+// every hi term, on one accumulator: the lo sum must be present before the
+// hi terms are rounded (added to an already rounded hi sum it is below half
+// a unit in the last place and is lost, and the FP32 rounding of U then
+// drifts the norm coherently).
+__device__ __forceinline__ void cmac(float2 &acc, const float2 u, const float2 v) {
+    acc.x = fmaf(u.x, v.x, acc.x);
+    acc.x = fmaf(-u.y, v.y, acc.x);
+    acc.y = fmaf(u.x, v.y, acc.y);
+    acc.y = fmaf(u.y, v.x, acc.y);
+}
+// In registers, a coefficient is expanded to the pairs (u.x, u.x) and (-u.y,
+// u.y) for packed FMAs: with v = (re, im) and vs = (im, re),
+// acc += u v is re += u.x re - u.y im, im += u.x im + u.y re, the same
+// roundings as cmac.
+struct Pk {
+    f2p xx, yy;
+};
+__device__ __forceinline__ Pk pk_coef(const float2 u) { return Pk{pack2(u.x, u.x), pack2(-u.y, u.y)}; }
+__device__ __forceinline__ f2p pmac(f2p acc, const Pk &c, f2p v, f2p vs) {
+    acc = fma2(c.xx, v, acc);
+    return fma2(c.yy, vs, acc);
+}
+
+// Dense gate of dimension D on the tile in shared memory; hi, lo: D x D
+// coefficient blocks, row-major.  Each specialisation is its own function
+// (called once per gate and tile), so that the register demand of the large
+// ones stays out of the kernel body.  D <= 3: coefficients held in registers,
+// packed FMAs (two groups per iteration for D = 2); D <= 8: rows fully
+// unrolled, offsets in registers; larger D: one row at a time (bounded code).
 template <int D>
-__device__ __noinline__ void dense_tile(const BGate &G, float2 *st, const float2 *cf) {
-    constexpr bool kRegOff = D <= 10;
-    uint32_t off[kRegOff ? D : 1];
-    if (kRegOff) {
+__device__ __noinline__ void dense_tile(const BGate &G, float2 *st, const float2 *hi) {
+    const float2 *lo = hi + D * D;
+    constexpr bool kSmall = D <= 8;
+    uint32_t off[kSmall ? D : 1];
+    if (kSmall) {
 #pragma unroll
-        for (int j = 0; j < D; ++j) off[kRegOff ? j : 0] = G.off[j];
+        for (int j = 0; j < D; ++j) off[kSmall ? j : 0] = G.off[j];
     }
-#define QD_OFF(j) (kRegOff ? off[kRegOff ? (j) : 0] : (uint32_t)G.off[j])
-    const float2 *hi = cf, *lo = cf + D * D;
-    for (uint32_t r = threadIdx.x; r < G.R; r += blockDim.x) {
-        const uint32_t base = expand(r, G.ex) + G.base;
-        float2 v[D];
+#define QD_OFF(j) (kSmall ? off[kSmall ? (j) : 0] : (uint32_t)G.off[j])
+    if constexpr (D <= 3) {
+        constexpr uint32_t P = D <= 2 ? 2 : 1;
+        Pk ch[D * D], cl[D * D];
 #pragma unroll
-        for (int j = 0; j < D; ++j) v[j] = st[base + QD_OFF(j)];
+        for (int k = 0; k < D * D; ++k) {
+            ch[k] = pk_coef(hi[k]);
+            cl[k] = pk_coef(lo[k]);
+        }
+        for (uint32_t r0 = threadIdx.x; r0 < G.R; r0 += P * blockDim.x) {
+            uint32_t base[P];
+            bool ok[P];
+            f2p v[P][D], vs[P][D];
 #pragma unroll
-        for (int i = 0; i < D; ++i) {
-            float2 acc = make_float2(0.f, 0.f);
+            for (uint32_t p = 0; p < P; ++p) {
+                const uint32_t r = r0 + p * blockDim.x;
+                ok[p] = r < G.R;
+                base[p] = ok[p] ? expand(r, G.ex) + G.base : 0;
 #pragma unroll
-            for (int j = 0; j < D; ++j) cmac(acc, lo[i * D + j], v[j]);
+                for (int j = 0; j < D; ++j) {
+                    const float2 a = ok[p] ? st[base[p] + off[j]] : make_float2(0.f, 0.f);
+                    v[p][j] = pack2(a.x, a.y);
+                    vs[p][j] = pack2(a.y, a.x);
+                }
+            }
 #pragma unroll
-            for (int j = 0; j < D; ++j) cmac(acc, hi[i * D + j], v[j]);
-            st[base + QD_OFF(i)] = acc;
+            for (int i = 0; i < D; ++i) {
+#pragma unroll
+                for (uint32_t p = 0; p < P; ++p) {
+                    f2p acc = 0ull;
+#pragma unroll
+                    for (int j = 0; j < D; ++j) acc = pmac(acc, cl[i * D + j], v[p][j], vs[p][j]);
+#pragma unroll
+                    for (int j = 0; j < D; ++j) acc = pmac(acc, ch[i * D + j], v[p][j], vs[p][j]);
+                    if (ok[p]) st[base[p] + off[i]] = unpack2(acc);
+                }
+            }
+        }
+    } else {
+        for (uint32_t r = threadIdx.x; r < G.R; r += blockDim.x) {
+            const uint32_t base = expand(r, G.ex) + G.base;
+            float2 v[D];
+#pragma unroll
+            for (int j = 0; j < D; ++j) v[j] = st[base + QD_OFF(j)];
+            if (kSmall) {
+#pragma unroll
+                for (int i = 0; i < D; ++i) {
+                    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int j = 0; j < D; ++j) cmac(acc, lo[i * D + j], v[j]);
+#pragma unroll
+                    for (int j = 0; j < D; ++j) cmac(acc, hi[i * D + j], v[j]);
+                    st[base + QD_OFF(i)] = acc;
+                }
+            } else {
+#pragma unroll 1
+                for (int i = 0; i < D; ++i) {
+                    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int j = 0; j < D; ++j) cmac(acc, lo[i * D + j], v[j]);
+#pragma unroll
+                    for (int j = 0; j < D; ++j) cmac(acc, hi[i * D + j], v[j]);
+                    st[base + G.off[i]] = acc;
+                }
+            }
         }
     }
 }
 
 // Permutation with phases of dimension D: out[i] = lam[i] in[src[i]] for the
-// active i (lam[i] == 1 exactly where unit bit i is set).
+// active i (lam[i] == 1 exactly where unit bit i is set); hi, lo: D phases.
 template <int D>
-__device__ __noinline__ void mono_tile(const BGate &G, float2 *st, const float2 *cf) {
-    constexpr bool kRegOff = D <= 10;
-    uint32_t off[kRegOff ? D : 1], soff[kRegOff ? D : 1];  // soff[i] = off[src[i]]
-    if (kRegOff) {
+__device__ __noinline__ void mono_tile(const BGate &G, float2 *st, const float2 *hi) {
+    const float2 *lo = hi + D;
+    constexpr bool kSmall = D <= 8;
+    constexpr bool kRegLam = D <= 5;
+    uint32_t off[kSmall ? D : 1], soff[kSmall ? D : 1];  // soff[i] = off[src[i]]
+    if (kSmall) {
 #pragma unroll
         for (int j = 0; j < D; ++j) {
-            off[kRegOff ? j : 0] = G.off[j];
-            soff[kRegOff ? j : 0] = G.off[G.src[j]];
+            off[kSmall ? j : 0] = G.off[j];
+            soff[kSmall ? j : 0] = G.off[G.src[j]];
         }
     }
-#define QD_SOFF(i) (kRegOff ? soff[kRegOff ? (i) : 0] : (uint32_t)G.off[G.src[i]])
-    const float2 *hi = cf, *lo = cf + D;
+#define QD_SOFF(i) (kSmall ? soff[kSmall ? (i) : 0] : (uint32_t)G.off[G.src[i]])
     const uint32_t active = G.active, unit = G.unit;
-    for (uint32_t r = threadIdx.x; r < G.R; r += blockDim.x) {
-        const uint32_t base = expand(r, G.ex) + G.base;
-        float2 v[D];
+    Pk lh[kRegLam ? D : 1], ll[kRegLam ? D : 1];
+    if (kRegLam) {
 #pragma unroll
-        for (int i = 0; i < D; ++i)
-            v[i] = ((active >> i) & 1u) ? st[base + QD_SOFF(i)] : make_float2(0.f, 0.f);
+        for (int j = 0; j < D; ++j) {
+            lh[kRegLam ? j : 0] = pk_coef(hi[j]);
+            ll[kRegLam ? j : 0] = pk_coef(lo[j]);
+        }
+    }
+    constexpr uint32_t P = D <= 5 ? 2 : 1;
+    for (uint32_t r0 = threadIdx.x; r0 < G.R; r0 += P * blockDim.x) {
+        uint32_t base[P];
+        bool ok[P];
+        float2 v[P][D];
 #pragma unroll
-        for (int i = 0; i < D; ++i) {
-            if ((active >> i) & 1u) {
-                float2 o = v[i];
-                if (!((unit >> i) & 1u)) {
-                    float2 acc = make_float2(0.f, 0.f);
-                    cmac(acc, lo[i], v[i]);
-                    cmac(acc, hi[i], v[i]);
-                    o = acc;
+        for (uint32_t p = 0; p < P; ++p) {
+            const uint32_t r = r0 + p * blockDim.x;
+            ok[p] = r < G.R;
+            base[p] = ok[p] ? expand(r, G.ex) + G.base : 0;
+#pragma unroll
+            for (int i = 0; i < D; ++i)
+                v[p][i] = (ok[p] && ((active >> i) & 1u)) ? st[base[p] + QD_SOFF(i)] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (uint32_t p = 0; p < P; ++p) {
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                if (ok[p] && ((active >> i) & 1u)) {
+                    float2 o = v[p][i];
+                    if (!((unit >> i) & 1u)) {
+                        if (kRegLam) {
+                            const f2p w = pack2(o.x, o.y), ws = pack2(o.y, o.x);
+                            o = unpack2(pmac(pmac(0ull, ll[kRegLam ? i : 0], w, ws), lh[kRegLam ? i : 0], w, ws));
+                        } else {
+                            float2 acc = make_float2(0.f, 0.f);
+                            cmac(acc, lo[i], o);
+                            cmac(acc, hi[i], o);
+                            o = acc;
+                        }
+                    }
+                    st[base[p] + QD_OFF(i)] = o;
                 }
-                st[base + QD_OFF(i)] = o;
             }
         }
     }
@@ -146,9 +261,9 @@ __device__ __noinline__ void mono_tile(const BGate &G, float2 *st, const float2 
 #undef QD_SOFF
 
 // Any D <= kBatchMaxD (dimensions that no specialisation covers).
-__device__ __noinline__ void generic_tile(const BGate &G, float2 *st, const float2 *cf) {
+__device__ __noinline__ void generic_tile(const BGate &G, float2 *st, const float2 *hi) {
     const int D = G.D;
-    const float2 *hi = cf, *lo = cf + G.ncoef;
+    const float2 *lo = hi + G.ncoef;
     for (uint32_t r = threadIdx.x; r < G.R; r += blockDim.x) {
         const uint32_t base = expand(r, G.ex) + G.base;
         float2 v[kBatchMaxD];
@@ -168,8 +283,8 @@ __device__ __noinline__ void generic_tile(const BGate &G, float2 *st, const floa
                     float2 o = v[i];
                     if (!((G.unit >> i) & 1u)) {
                         float2 acc = make_float2(0.f, 0.f);
-                        cmac(acc, lo[i], v[i]);
-                        cmac(acc, hi[i], v[i]);
+                        cmac(acc, lo[i], o);
+                        cmac(acc, hi[i], o);
                         o = acc;
                     }
                     st[base + G.off[i]] = o;
@@ -205,12 +320,12 @@ __device__ __forceinline__ void apply_gate(const BGate &G, float2 *st, const flo
 #undef QD_BATCH_CASE
 }
 
-// Gather (LOAD) or scatter one tile between the state and shared memory, 16
+// Gather (LOAD) or scatter one tile between the state and shared memory, 8
 // independent accesses in flight per thread.
 template <bool LOAD>
 __device__ __forceinline__ void move_tile(float2 *psi, float2 *st, const BSeg &S, uint32_t tb,
                                           const uint32_t *__restrict__ hoff) {
-    constexpr int U = 16;
+    constexpr int U = 8;
     const uint32_t T = S.T, B = S.B;
     const FastDiv32 divB = S.divB;
     auto flat = [&](uint32_t l) {
@@ -234,15 +349,16 @@ __device__ __forceinline__ void move_tile(float2 *psi, float2 *st, const BSeg &S
     }
 }
 
-__global__ void __launch_bounds__(kBThreads, 4)
+__global__ void __launch_bounds__(kBThreads, 5)
     k_batch(float2 *__restrict__ arena, const uint64_t *__restrict__ offs, const BSeg *__restrict__ segs,
             const BChunk *__restrict__ chunks, const BGate *__restrict__ gates, const float2 *__restrict__ coef,
             const uint32_t *__restrict__ hofftab, const BItem *__restrict__ items, int32_t nitems,
-            uint32_t *__restrict__ next, uint32_t *__restrict__ done, int32_t *__restrict__ err) {
+            uint32_t *__restrict__ next, uint32_t *__restrict__ done, int32_t *__restrict__ err,
+            uint32_t desc_bytes) {
     extern __shared__ __align__(16) unsigned char smraw[];
     BSeg &S = *reinterpret_cast<BSeg *>(smraw);
     unsigned char *desc = smraw + ((sizeof(BSeg) + 15) / 16) * 16;
-    float2 *st = reinterpret_cast<float2 *>(desc + kBatchDescBytes);
+    float2 *st = reinterpret_cast<float2 *>(desc + desc_bytes);
     __shared__ BChunk s_ch;
     __shared__ int32_t s_item;
     __shared__ int32_t s_ok;
@@ -297,7 +413,7 @@ __global__ void __launch_bounds__(kBThreads, 4)
                         // descriptor sanity: a gate's groups stay inside the tile and its
                         // coefficients inside the chunk (else: error word, gate skipped)
                         if (G.D >= 2 && G.D <= kBatchMaxD && (uint64_t)G.R * (uint32_t)G.D <= S.T &&
-                            ng * sizeof(BGate) + (size_t)(G.coef + 2 * G.ncoef) * sizeof(float2) <= kBatchDescBytes)
+                            ng * sizeof(BGate) + (size_t)(G.coef + 2 * G.ncoef) * sizeof(float2) <= desc_bytes)
                             apply_gate(G, st, sc + G.coef);
                         else if (threadIdx.x == 0)
                             atomicExch(err, 3);
@@ -330,12 +446,12 @@ __global__ void k_batch_ones(float2 *arena, const uint64_t *offs, const uint64_t
 
 }  // namespace
 
-size_t batch_smem_bytes(uint32_t tile_cap) {
-    return ((sizeof(BSeg) + 15) / 16) * 16 + kBatchDescBytes + (size_t)tile_cap * sizeof(float2);
+size_t batch_smem_bytes(uint32_t tile_cap, uint32_t desc_bytes) {
+    return ((sizeof(BSeg) + 15) / 16) * 16 + desc_bytes + (size_t)tile_cap * sizeof(float2);
 }
 
-int batch_occupancy(uint32_t tile_cap) {
-    const size_t smem = batch_smem_bytes(tile_cap);
+int batch_occupancy(uint32_t tile_cap, uint32_t desc_bytes) {
+    const size_t smem = batch_smem_bytes(tile_cap, desc_bytes);
     if (cudaFuncSetAttribute((const void *)k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess) {
         cudaGetLastError();
@@ -355,13 +471,13 @@ cudaError_t batch_launch(const BatchLaunch &b, cudaStream_t s, cudaEvent_t ev0, 
     k_batch_init<<<b.sm_count * 4, 256, 0, s>>>(b.arena, b.total);
     k_batch_ones<<<(b.ncirc + 255) / 256, 256, 0, s>>>(b.arena, b.offs, b.basis, b.ncirc);
     if (b.nitems > 0) {
-        const size_t smem = batch_smem_bytes(b.tile_cap);
-        const int occ = std::max(1, batch_occupancy(b.tile_cap));
+        const size_t smem = batch_smem_bytes(b.tile_cap, b.desc_bytes);
+        const int occ = std::max(1, batch_occupancy(b.tile_cap, b.desc_bytes));
         const int per_sm = b.ctas_per_sm > 0 && b.ctas_per_sm < occ ? b.ctas_per_sm : occ;
         const int grid = b.sm_count * per_sm;
         if (ev0) cudaEventRecord(ev0, s);
         k_batch<<<grid, kBThreads, smem, s>>>(b.arena, b.offs, b.segs, b.chunks, b.gates, b.coef, b.hoff, b.items,
-                                             b.nitems, b.counters, b.counters + 1, b.err);
+                                             b.nitems, b.counters, b.counters + 1, b.err, b.desc_bytes);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         if (ev1) cudaEventRecord(ev1, s);

@@ -13,7 +13,7 @@ constexpr int kBatchMaxD = 25;          // largest target dimension of a batched
 constexpr uint32_t kBatchMaxTile = 24576;  // largest tile (amplitudes) kept in shared memory
 
 constexpr int kBExMax = 8;              // insertion runs of a tile-local gate (<= 14 local qudits)
-constexpr uint32_t kBatchDescBytes = 16384;  // shared memory for one chunk of gate descriptors + coefficients
+constexpr uint32_t kBatchDescBytes = 8192;  // target size of one chunk (a single larger gate is its own chunk)
 
 // Insert-digit expansion with at most kBExMax runs (adjacent removed qudits
 // merged into one run).
@@ -39,7 +39,7 @@ __host__ __device__ __forceinline__ uint32_t expand(uint32_t r, const BEx &e) {
 // One gate in the local index space of its segment's tile (32-bit direct
 // geometry): dense (kind 0, D x D coefficients) or a permutation with phases
 // (kind 1, D phases).  Coefficients: ncoef FP32 "hi" entries at coef (float2
-// offset inside its chunk's coefficient block), then ncoef "lo" entries.
+// offset inside its chunk's coefficient block, even), then ncoef "lo" entries.
 struct __align__(16) BGate {
     int32_t kind;
     int32_t D;
@@ -106,14 +106,15 @@ struct BatchLaunch {
     int sm_count;
     int ctas_per_sm;     // 0: as many as fit
     uint32_t tile_cap;   // largest tile of any segment (shared-memory amplitudes)
+    uint32_t desc_bytes; // shared-memory area for one chunk (>= every chunk, multiple of 16)
 };
 
-size_t batch_smem_bytes(uint32_t tile_cap);
+size_t batch_smem_bytes(uint32_t tile_cap, uint32_t desc_bytes);
 // Enqueue: reset the counters and every state to its basis state, the
 // persistent kernel, and the FP64 probabilities of the whole arena.  When
 // ev0/ev1 are given they are recorded around the persistent kernel.
 cudaError_t batch_launch(const BatchLaunch &b, cudaStream_t s, cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr);
 // Resident CTAs per SM of the persistent kernel for a tile capacity.
-int batch_occupancy(uint32_t tile_cap);
+int batch_occupancy(uint32_t tile_cap, uint32_t desc_bytes);
 
 }  // namespace qd

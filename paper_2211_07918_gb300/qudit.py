@@ -109,6 +109,7 @@ _SIGS = {
     "qd_batch_info": [_vp, _i64p, _i32p, _i32p, _i32p],
     "qd_batch_profile": [_vp, _i32],
     "qd_batch_timings": [_vp, ctypes.POINTER(ctypes.c_float), _dp],
+    "qd_batch_autotune": [_vp, _i32, _i64p, ctypes.POINTER(ctypes.c_float)],
     "qd_batch_destroy": [_vp],
 }
 
@@ -705,6 +706,15 @@ def qd_batch_timings(batch: int, with_time: bool = True):
     ms, ab = ctypes.c_float(), ctypes.c_double()
     _check(load().qd_batch_timings(_vp(batch), ctypes.byref(ms) if with_time else None, ctypes.byref(ab)))
     return (ms.value if with_time else None), ab.value
+
+
+def qd_batch_autotune(batch: int, reps: int = 2) -> dict:
+    """Pick the fastest launch shape (see include/qudit.h); returns it."""
+    ch = np.zeros(4, dtype=np.int64)
+    ms = ctypes.c_float()
+    _check(load().qd_batch_autotune(_vp(batch), reps, ch.ctypes.data_as(_i64p), ctypes.byref(ms)))
+    return {"tile_amps": int(ch[0]), "small_amps": int(ch[1]), "ctas_per_sm": int(ch[2]),
+            "tiles_per_item": int(ch[3]), "kernel_ms": ms.value}
 
 
 def qd_batch_destroy(batch: int) -> None:

@@ -101,6 +101,41 @@ def test_batch_long_circuits_many_chunks():
             check_circuit(d, g, psi, p)
 
 
+def test_batch_long_circuit_precision():
+    # 1000 gates, two thirds dense: the FP32 hi + lo coefficient split must
+    # keep the norm (a lost lo part drifts it coherently by ~1.5e-9 per gate)
+    mix = ("H", "U1", "U2", "X", "CX", "U1")
+    circuits = []
+    for c in range(6):
+        rng = np.random.default_rng(9500 + c)
+        d = [int(x) for x in rng.choice((2, 3, 4, 5), size=5)]
+        circuits.append((d, [wl.random_gate(rng, d, mix) for _ in range(1000)]))
+    for tune in ((), ((L.QD_BATCH_SMALL_AMPS, 0), (L.QD_BATCH_TILE_AMPS, 128))):
+        amps, probs, info = run_batch(circuits, tune)
+        assert info["device_error"] == 0
+        for (d, g), psi, p in zip(circuits, amps, probs):
+            assert abs(float(np.sum(p)) - 1.0) <= 1e-6
+            check_circuit(d, g, psi, p)
+
+
+def test_batch_autotune_keeps_results():
+    circuits = mixed_batch(9400, 12, 40, nmin=4, nmax=9)
+    b = L.qd_batch_create([d for d, _ in circuits])
+    try:
+        for c, (_, g) in enumerate(circuits):
+            L.qd_batch_set_circuit(b, c, g)
+        best = L.qd_batch_autotune(b, 1)
+        assert best["tile_amps"] in (2048, 4096, 6144, 8192) and best["kernel_ms"] > 0
+        L.qd_batch_run(b)
+        assert L.qd_batch_info(b, with_error=True)["device_error"] == 0
+        for c, (d, g) in enumerate(circuits):
+            N = int(np.prod(d))
+            check_circuit(d, g, L.qd_batch_get_amplitudes(b, c, N).astype(np.complex128),
+                          L.qd_batch_probabilities(b, c, N))
+    finally:
+        L.qd_batch_destroy(b)
+
+
 def test_batch_graph_replay_on_stream():
     torch = pytest.importorskip("torch")
     circuits = mixed_batch(9200, 12, 30, nmin=3, nmax=8)
