@@ -45,12 +45,16 @@ def parse():
     ap.add_argument("--cpu-sample-gates", type=int, default=0, help="gates in the CPU-baseline sample (0: auto)")
     ap.add_argument("--c2-ququarts", type=int, default=12,
                     help="ququarts of the c2 register (12: the full 2^32-amplitude case; fewer for profiling)")
-    ap.add_argument("--workload", default="c1", choices=["c1", "c2", "c3"],
+    ap.add_argument("--c3-circuits", type=int, default=256,
+                    help="circuits of the c3 batch (256: the full workload; fewer for profiling)")
+    ap.add_argument("--workload", default="c1", choices=["c1", "c2", "c3", "c4"],
                     help="c1: 14 qutrits, 500 gates, per-gate kernels (default); "
                          "c2: 8 qubits + 12 ququarts (2^32 amplitudes), Haar layer + d=4 QFT + Toffoli ladder, "
                          "fused tensor-core blocks vs the FP64 per-gate path; "
                          "c3: 256 independent circuits (6-12 qudits, dims 2..5, 200 gates each) in one persistent "
-                         "graph-captured launch vs one graph-captured plan per circuit")
+                         "graph-captured launch vs one graph-captured plan per circuit; "
+                         "c4: 18 qutrits + 4 qubits (6.2e9 amplitudes), 1,000-gate circuit, fusion planned with "
+                         "the learned cost model vs the greedy and exhaustive analytic plans and per-gate kernels")
     return ap.parse_args()
 
 
@@ -125,37 +129,50 @@ class ClockSampler:
 
 
 KERNEL_SOURCES = ("qd_apply.cuh", "qd_common.cuh", "qd_plan.h")
+BATCH_SOURCES = ("qd_batch.cu", "qd_batch.h", "qd_common.cuh")
 
 
-def kernel_source_sha():
-    """Hash of the per-gate kernel sources (the dominant kernel's code)."""
+def kernel_source_sha(files=KERNEL_SOURCES):
+    """Hash of a kernel's sources (a committed ncu figure is used only while
+    the sources it was taken on are unchanged)."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2211_07918_gb300", "csrc")
-    for f in KERNEL_SOURCES:
+    for f in files:
         with open(os.path.join(d, f), "rb") as fh:
             h.update(f.encode())
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kname: str):
-    """dram bytes per launch for kernel class ``kname`` from a committed ncu
-    summary in profiles/, or None if absent or taken on different sources."""
+def _profile_fields(kname: str, files):
     pdir = os.path.join(ROOT, "profiles")
     if not os.path.isdir(pdir):
         return None
-    sha = kernel_source_sha()
+    sha = kernel_source_sha(files)
     for f in sorted(os.listdir(pdir)):
         if not f.endswith(".md"):
             continue
         with open(os.path.join(pdir, f)) as fh:
             txt = fh.read()
-        m = re.search(r"^traffic_kernel_class:\s*(\S+)", txt, re.M)
-        t = re.search(r"^traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt, re.M)
-        s = re.search(r"^source_sha:\s*(\S+)", txt, re.M)
-        if m and t and s and m.group(1) == kname and s.group(1) == sha:
-            return float(t.group(1))
+        fields = dict(re.findall(r"^(traffic_[a-z_]+|source_sha):\s*(\S+)", txt, re.M))
+        if fields.get("traffic_kernel_class") == kname and fields.get("source_sha") == sha:
+            return fields
     return None
+
+
+def profiled_traffic(kname: str):
+    """dram bytes per launch for kernel class ``kname`` from a committed ncu
+    summary in profiles/, or None if absent or taken on different sources."""
+    f = _profile_fields(kname, KERNEL_SOURCES)
+    return float(f["traffic_bytes_per_launch"]) if f and "traffic_bytes_per_launch" in f else None
+
+
+def profiled_traffic_scaled(kname: str, alg_bytes: float, files=BATCH_SOURCES):
+    """dram bytes of a full launch from a capture of a smaller case of the
+    same kernel: the captured dram bytes per algorithmic byte times this
+    launch's algorithmic bytes (the kernel's traffic grows with the work)."""
+    f = _profile_fields(kname, files)
+    return float(f["traffic_per_alg_byte"]) * alg_bytes if f and "traffic_per_alg_byte" in f else None
 
 
 # ------------------------------------------------------------- CPU baseline
@@ -370,7 +387,7 @@ def run_c3(args, rank, world, local):
     L.load()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    circuits = wl.batch_c3()
+    circuits = wl.batch_c3()[: args.c3_circuits]
     regs = [d for d, _ in circuits]
     Ns = [int(np.prod(d)) for d in regs]
     total = sum(Ns)
@@ -465,7 +482,9 @@ def run_c3(args, rank, world, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD_C3, "circuits": len(circuits), "amplitudes": total, "gates": ngates,
+        "config": {"workload": WORKLOAD_C3 if len(circuits) == 256 else
+                   f"the first {len(circuits)} circuits of the c3 batch (profiling size)",
+                   "circuits": len(circuits), "amplitudes": total, "gates": ngates,
                    "precision": "complex64", "l2": "flushed (256 MiB write) before every timed step; "
                    "states (1.95 GB) larger than L2",
                    "step": "reset all registers + all circuits + FP64 probabilities of every register"},
@@ -476,7 +495,8 @@ def run_c3(args, rank, world, local):
                     "per_circuit_plans_gates_per_s": world * ngates / (float(np.mean(ms_per)) * 1e-3),
                     "batch_over_per_circuit": float(np.mean(ms_per)) / ms_step},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "kernel": "k_batch", "peak_source": peak_src,
+                     "traffic": profiled_traffic_scaled("k_batch", alg_bytes), "kernel": "k_batch",
+                     "peak_source": peak_src,
                      "alg_bytes_per_launch": alg_bytes,
                      "note": "large circuits run in groups whose states stay in L2; achieved can exceed HBM peak"},
         "clocks": clocks,
@@ -485,6 +505,117 @@ def run_c3(args, rank, world, local):
                 "path": "qd_batch_set_circuit x256 (host gates) + qd_batch_run + qd_batch_probabilities x256 (host)"},
         "gpu_launches": int(args.steps * info["launches"]),
         "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+WORKLOAD_C4 = ("18 qutrits + 4 qubits (3^18 * 2^4 = 6,198,727,824 amplitudes, 49.6 GB complex64), "
+               "1,000-gate random circuit (X, Z, F_d, CX_d, Haar-1, Haar-2), fusion planned with the learned "
+               "MLP cost model (weights trained on GB300 launch timings)")
+
+
+def run_c4(args, rank, world, local):
+    """Learned fusion planning at scale: the plan chosen with the learned
+    cost model against the greedy and exhaustive plans of the analytic model
+    and against per-gate kernels, on the same complex64 register; fidelity of
+    the learned plan's state against the per-gate state through qd_overlap."""
+    import torch
+
+    from paper_2211_07918_gb300 import costmodel as cm
+    from paper_2211_07918_gb300 import qudit as L
+    from paper_2211_07918_gb300 import workloads as wl
+    from paper_2211_07918_gb300.build import build
+
+    build()
+    L.load()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dims, gates = wl.circuit_c4()
+    N = int(np.prod(dims))
+    ngates = len(gates)
+    stream = torch.cuda.Stream(device=dev)
+    model = cm.load()
+    reg = L.qd_create(dims, None, L.QD_C64, 0, 0, stream.cuda_stream)
+    L.qd_set_cost_model(reg, model)
+
+    def timed(plan, steps, warmup):
+        for _ in range(warmup):
+            L.qd_reset(reg)
+            L.qd_plan_run(plan)
+        stream.synchronize()
+        ts = []
+        for _ in range(steps):
+            L.qd_reset(reg)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            L.qd_plan_run(plan)
+            b.record(stream)
+            stream.synchronize()
+            ts.append(a.elapsed_time(b))
+        return ts
+
+    res, plans = {}, {}
+    for name, kind in (("learned", L.QD_PLAN_LEARNED), ("greedy", L.QD_PLAN_GREEDY),
+                       ("exhaustive_analytic", L.QD_PLAN_EXHAUSTIVE), ("per_gate", L.QD_PLAN_NONE)):
+        t0 = time.perf_counter()
+        plans[name] = L.qd_plan_create(reg, gates, kind)
+        res[name] = {"plan_s": time.perf_counter() - t0}
+    sampler = ClockSampler(local)
+    sampler.start()
+    for name in plans:
+        steps = args.steps if name == "learned" else max(1, args.steps // 2)
+        ts = timed(plans[name], steps, 1)
+        info = L.qd_plan_info(plans[name])
+        res[name].update({"ms_per_step": float(np.mean(ts)), "gates_per_s": ngates / (float(np.mean(ts)) * 1e-3),
+                          "launches": info["launches"], "blocks": info["blocks"]})
+    clocks = sampler.stop()
+    # per-kernel times of the learned plan (per-launch events)
+    L.qd_plan_profile(plans["learned"], True)
+    L.qd_reset(reg)
+    L.qd_plan_run(plans["learned"])
+    ms, ab, kc = L.qd_plan_timings(plans["learned"])
+    kern = {}
+    for t, b_, c in zip(ms, ab, kc):
+        k = kern.setdefault(L.kclass_name(int(c)), [0.0, 0.0, 0])
+        k[0] += float(t)
+        k[1] += float(b_)
+        k[2] += 1
+    # fidelity: learned plan (fused) vs per-gate kernels, both complex64
+    L.qd_reset(reg)
+    L.qd_plan_run(plans["learned"])
+    ref = L.qd_create(dims, None, L.QD_C64, 0, 0, stream.cuda_stream)
+    plan_ref = L.qd_plan_create(ref, gates, L.QD_PLAN_NONE)
+    L.qd_plan_run(plan_ref)
+    ov = L.qd_overlap(ref, reg)
+    n_fused, n_ref = L.qd_norm(reg), L.qd_norm(ref)
+    for p_ in plans.values():
+        L.qd_plan_destroy(p_)
+    L.qd_plan_destroy(plan_ref)
+    L.qd_destroy(ref)
+    L.qd_destroy(reg)
+    L.qd_model_destroy(model)
+    kname, kdata = max(kern.items(), key=lambda kv: kv[1][0])
+    peak, peak_src = measured_peaks()
+    achieved = kdata[1] / (kdata[0] * 1e-3) / 1e9
+    value = world * res["learned"]["gates_per_s"]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": 1,
+        "ms_per_step": res["learned"]["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD_C4, "amplitudes": N, "gates": ngates, "precision": "complex64",
+                   "l2": "inputs (49.6 GB) larger than L2", "step": "reset + planned circuit"},
+        "amp_updates_per_s": value * N,
+        "compare": {**{k: v for k, v in res.items()},
+                    "learned_over_greedy": res["greedy"]["ms_per_step"] / res["learned"]["ms_per_step"],
+                    "learned_over_per_gate": res["per_gate"]["ms_per_step"] / res["learned"]["ms_per_step"],
+                    "fidelity_learned_vs_per_gate_c64": abs(ov) ** 2, "norm2_learned": n_fused, "norm2_per_gate": n_ref},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": kname, "peak_source": peak_src,
+                     "share_of_gate_time": kdata[0] / sum(v[0] for v in kern.values()), "launches": kdata[2]},
+        "kernels": {k: {"ms": v[0], "launches": v[2], "GB_s": v[1] / (v[0] * 1e-3) / 1e9} for k, v in kern.items()},
+        "clocks": clocks,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -691,6 +822,8 @@ def main():
         return run_c2(args, rank, world, local)
     if args.workload == "c3":
         return run_c3(args, rank, world, local)
+    if args.workload == "c4":
+        return run_c4(args, rank, world, local)
     return run_ours(args, rank, world, local)
 
 
