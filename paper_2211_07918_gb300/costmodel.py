@@ -34,6 +34,13 @@ TRAIN_REGISTERS = (
 )
 
 
+# Registers above 2^31 amplitudes (64-bit index kernels; 34-50 GB complex64).
+LARGE_REGISTERS = (
+    [3] * 18 + [2] * 4,  # 6.2e9
+    [2] * 8 + [4] * 12,  # 4.3e9
+)
+
+
 def register_size(dims: Sequence[int]) -> int:
     return int(np.prod([int(d) for d in dims]))
 
@@ -247,13 +254,31 @@ def main(argv=None):
     ap.add_argument("--out", default=DEFAULT_WEIGHTS)
     ap.add_argument("--circuits", type=int, default=4)
     ap.add_argument("--no-judge", action="store_true")
+    ap.add_argument("--large-samples", type=int, default=0,
+                    help="extra samples on registers above 2^31 amplitudes (64-bit index kernels)")
+    ap.add_argument("--base-data", default=None,
+                    help="npz (X, y) of earlier samples to train on together with the new ones")
     args = ap.parse_args(argv)
     from .build import build
     build()
     L.load()
     log = lambda m: print(m, flush=True)  # noqa: E731
     t0 = time.time()
-    X, y = generate(args.samples, args.seed, log=log)
+    parts_X, parts_y = [], []
+    if args.base_data:
+        d = np.load(args.base_data)
+        parts_X.append(d["X"])
+        parts_y.append(d["y"])
+        log(f"base data: {len(d['y'])} samples")
+    if args.samples > 0:
+        X, y = generate(args.samples, args.seed, log=log)
+        parts_X.append(X)
+        parts_y.append(y)
+    if args.large_samples > 0:
+        X, y = generate(args.large_samples, args.seed + 1, registers=LARGE_REGISTERS, reps=2, log=log)
+        parts_X.append(X)
+        parts_y.append(y)
+    X, y = np.concatenate(parts_X), np.concatenate(parts_y)
     gen_s = time.time() - t0
     n = len(y)
     idx = np.random.default_rng(args.seed).permutation(n)
