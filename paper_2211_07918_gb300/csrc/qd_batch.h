@@ -25,13 +25,11 @@ struct BEx {
 };
 
 __host__ __device__ __forceinline__ uint32_t expand(uint32_t r, const BEx &e) {
-#pragma unroll
-    for (int k = 0; k < kBExMax; ++k) {
-        if (k < e.n) {
-            const uint32_t q = fdiv(r, e.div[k]);
-            const uint32_t lo = r - q * e.div[k].d;
-            r = q * e.span[k] + lo;
-        }
+#pragma unroll 1
+    for (int k = 0; k < e.n; ++k) {
+        const uint32_t q = fdiv(r, e.div[k]);
+        const uint32_t lo = r - q * e.div[k].d;
+        r = q * e.span[k] + lo;
     }
     return r;
 }

@@ -105,14 +105,15 @@ struct Expand64 {
     uint64_t span[kMaxIns];
 };
 
+// The loops run over the insertions actually present (e.n is uniform across
+// a launch): a loop unrolled to kMaxIns with a predicate per step would issue
+// every predicated-off step as well.
 __host__ __device__ __forceinline__ uint64_t expand(uint64_t r, const Expand64 &e) {
-#pragma unroll
-    for (int k = 0; k < kMaxIns; ++k) {
-        if (k < e.n) {
-            const uint64_t q = fdiv(r, e.div[k]);
-            const uint64_t lo = r - q * e.div[k].d;
-            r = q * e.span[k] + lo;
-        }
+#pragma unroll 1
+    for (int k = 0; k < e.n; ++k) {
+        const uint64_t q = fdiv(r, e.div[k]);
+        const uint64_t lo = r - q * e.div[k].d;
+        r = q * e.span[k] + lo;
     }
     return r;
 }
@@ -125,13 +126,11 @@ struct Expand32 {
 };
 
 __host__ __device__ __forceinline__ uint32_t expand(uint32_t r, const Expand32 &e) {
-#pragma unroll
-    for (int k = 0; k < kMaxIns; ++k) {
-        if (k < e.n) {
-            const uint32_t q = fdiv(r, e.div[k]);
-            const uint32_t lo = r - q * e.div[k].d;
-            r = q * e.span[k] + lo;
-        }
+#pragma unroll 1
+    for (int k = 0; k < e.n; ++k) {
+        const uint32_t q = fdiv(r, e.div[k]);
+        const uint32_t lo = r - q * e.div[k].d;
+        r = q * e.span[k] + lo;
     }
     return r;
 }
