@@ -20,6 +20,7 @@
 //           tile, and writes the chunks back with coalesced stores.
 #pragma once
 #include <algorithm>
+#include <cstring>
 #include <type_traits>
 
 #include "qd_plan.h"
@@ -63,6 +64,35 @@ __device__ __forceinline__ v2<T> cmul_split(const v2<T> hi, const v2<T> lo, cons
     }
 }
 
+// Packed FP32 pairs (fma.rn.f32x2: two FMAs, each rounded as fmaf).  A
+// coefficient u is carried as the pairs (u.x, u.x) and (-u.y, u.y); with
+// v = (re, im) and vs = (im, re), acc += u v is two packed FMAs with the
+// roundings of cmac<float>.
+typedef unsigned long long f2p;
+__device__ __forceinline__ f2p pk_fma(f2p a, f2p b, f2p c) {
+    f2p d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f2p pk_pack(float a, float b) {
+    f2p r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float2 pk_unpack(f2p r) {
+    float a, b;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+    return make_float2(a, b);
+}
+inline unsigned long long pk_host(float a, float b) {
+    unsigned int ua, ub;
+    std::memcpy(&ua, &a, 4);
+    std::memcpy(&ub, &b, 4);
+    return (unsigned long long)ua | ((unsigned long long)ub << 32);
+}
+// Dense complex64 gates of up to 4 x 4 use the packed path.
+template <typename T, int MD> constexpr bool kPacked = kSplit<T> && MD <= 4;
+
 template <typename T>
 inline void split_coef(double re, double im, v2<T> &hi, v2<T> &lo) {
     hi = mk<T>((T)re, (T)im);
@@ -82,6 +112,8 @@ struct DenseDirectArgs {
     I off[MD];
     v2<T> U[MD * MD];  // row-major, zero-padded to MD x MD
     v2<T> Ulo[split_len<T>(MD * MD)];
+    // packed path: per coefficient lo (x,x), lo (-y,y), hi (x,x), hi (-y,y)
+    unsigned long long Pk[kPacked<T, MD> ? 4 * MD * MD : 1];
 };
 
 template <typename T, typename I, int MD>
@@ -157,6 +189,37 @@ __global__ void __launch_bounds__(256) k_dense_direct(const __grid_constant__ De
 #pragma unroll
             for (int j = 0; j < MD; ++j)
                 v[u][j] = (ok[u] && (EX || j < D)) ? a.psi[base[u] + a.off[j]] : mk<T>(T(0), T(0));
+        if constexpr (kPacked<T, MD>) {
+            // lo terms first, then hi terms (as below), two lanes per FMA
+#pragma unroll
+            for (int u = 0; u < UN; ++u) {
+                if (!ok[u]) continue;
+                f2p pv[MD], ps[MD];
+#pragma unroll
+                for (int j = 0; j < MD; ++j) {
+                    pv[j] = pk_pack(v[u][j].x, v[u][j].y);
+                    ps[j] = pk_pack(v[u][j].y, v[u][j].x);
+                }
+#pragma unroll
+                for (int i = 0; i < MD; ++i) {
+                    if (EX || i < D) {
+                        f2p acc = 0ull;
+#pragma unroll
+                        for (int j = 0; j < MD; ++j) {
+                            acc = pk_fma(a.Pk[4 * (i * MD + j) + 0], pv[j], acc);
+                            acc = pk_fma(a.Pk[4 * (i * MD + j) + 1], ps[j], acc);
+                        }
+#pragma unroll
+                        for (int j = 0; j < MD; ++j) {
+                            acc = pk_fma(a.Pk[4 * (i * MD + j) + 2], pv[j], acc);
+                            acc = pk_fma(a.Pk[4 * (i * MD + j) + 3], ps[j], acc);
+                        }
+                        const float2 o = pk_unpack(acc);
+                        a.psi[base[u] + a.off[i]] = mk<T>(o.x, o.y);
+                    }
+                }
+            }
+        } else {
 #pragma unroll
         for (int u = 0; u < UN; ++u) {
             if (!ok[u]) continue;
@@ -173,6 +236,7 @@ __global__ void __launch_bounds__(256) k_dense_direct(const __grid_constant__ De
                     a.psi[base[u] + a.off[i]] = acc;
                 }
             }
+        }
         }
     }
 }
@@ -410,6 +474,18 @@ cudaError_t launch_dense(const GatePlan &g, void *psi, int sm_count, cudaStream_
         a.ex = expand_for<I>(g.ex);
         for (int j = 0; j < MD; ++j) a.off[j] = j < g.D ? (I)g.off[j] : 0;
         fill_matrix<T, MD>(a.U, a.Ulo, g);
+        if constexpr (kPacked<T, MD>) {
+            for (int k = 0; k < MD * MD; ++k) {
+                const float hx = (float)a.U[k].x, hy = (float)a.U[k].y;
+                const float lx = (float)a.Ulo[k].x, ly = (float)a.Ulo[k].y;
+                a.Pk[4 * k + 0] = pk_host(lx, lx);
+                a.Pk[4 * k + 1] = pk_host(-ly, ly);
+                a.Pk[4 * k + 2] = pk_host(hx, hx);
+                a.Pk[4 * k + 3] = pk_host(-hy, hy);
+            }
+        } else {
+            a.Pk[0] = 0;
+        }
         auto fn = k_dense_direct<T, I, MD, EX>;
         const int grid = grid_of(g.R, kBlock, sm_count, occupancy_blocks((const void *)fn, kBlock, 0));
         if (grid <= 0) return cudaSuccess;
