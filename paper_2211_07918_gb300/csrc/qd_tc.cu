@@ -40,8 +40,12 @@
 //     acc_empty[a], issue the slice products into accumulator slot a of a
 //     2-slot TMEM ring, commit to acc_full[a];
 //   epilogue (warps 0..3, one TMEM lane per thread): wait acc_full[a], combine
-//     the levels, scatter the outputs, arrive acc_empty[a] (and empty[s] after
-//     the last half).
+//     the levels, scatter the outputs, arrive acc_empty[a].
+// A stage is released by a tcgen05.commit to empty[s] once its MMAs have
+// completed, so producers fill the next tile while the epilogue drains the
+// previous one; the per-row scales of a tile travel to the epilogue through
+// their own 2-deep ring (sc_full / sc_empty), which keeps every barrier at
+// most one phase ahead of its waiters.
 // Unit u = (tile i, half h) uses slot u % 2; tile i uses stage i % STAGES;
 // mbarrier phases count the reuses.  Every wait is bounded and also gives up
 // when another warp has raised the abort flag (the device error word is set);
@@ -166,9 +170,16 @@ template <int MAXD> struct TcCfg {
     static constexpr int XS = 3;                        // state slices
     static constexpr int NH = MAXD <= 32 ? 1 : 2;       // output halves
     static constexpr int STAGES = MAXD <= 32 ? 3 : 1;   // shared-memory ring
-    static constexpr int PW = MAXD <= 32 ? 8 : 4;       // producer warps
+    static constexpr int PW = MAXD <= 32 ? 8 : 4;       // producer warps (groups of 128 rows)
     static constexpr int THREADS = 32 * (5 + PW);
     static constexpr int NPAIRS = XS == 3 ? 6 : 5;
+    // Stage-release barriers: tile i's MMAs commit to empty[i % NE]; the
+    // writer of tile i waits for tile i - STAGES on empty[(i - STAGES) % NE].
+    // With one stage NE = 2 (one barrier per tile parity): should two
+    // producer groups share the stage, a group can then never wait on a
+    // barrier two phases behind its target, which a single barrier would
+    // alias through its parity.
+    static constexpr int NE = STAGES == 1 ? 2 : STAGES;
 };
 
 // Kernel arguments: direct-mode group geometry plus the matrix slices,
@@ -197,8 +208,10 @@ __global__ void __launch_bounds__(TcCfg<MAXD>::THREADS, 1) k_block_tc(const __gr
     const float *bscale = reinterpret_cast<const float *>(B + 3u * bbytes);
     const uint32_t bregion = (3u * bbytes + K * 4u + 1023u) & ~1023u;
     unsigned char *stages = sm + bregion;  // stage s: X1 | X2 (| X3) at s * XS * xbytes
-    __shared__ __align__(8) uint64_t full[C::STAGES], empty[C::STAGES], acc_full[2], acc_empty[2];
-    __shared__ int32_t erow[C::STAGES][kTcRows];
+    __shared__ __align__(8) uint64_t full[C::STAGES], empty[C::NE], acc_full[2], acc_empty[2];
+    // row scales of a tile: a 2-deep ring between producers and epilogue
+    __shared__ __align__(8) uint64_t sc_full[2], sc_empty[2];
+    __shared__ int32_t erow[2][kTcRows];
     __shared__ uint32_t tmem_base;
     __shared__ volatile int32_t abort_flag;
 
@@ -214,13 +227,18 @@ __global__ void __launch_bounds__(TcCfg<MAXD>::THREADS, 1) k_block_tc(const __gr
         for (uint32_t i = tid; i < n16; i += blockDim.x) dst[i] = src[i];
     }
     if (tid == 0) {
-        for (int q = 0; q < C::STAGES; ++q) {
+        for (int q = 0; q < C::STAGES; ++q)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&full[q])), "r"(kTcRows) : "memory");
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&empty[q])), "r"(kTcRows) : "memory");
-        }
+        // a stage is free once the MMAs reading it have completed (tcgen05.commit)
+        for (int q = 0; q < C::NE; ++q)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&empty[q])) : "memory");
         for (int q = 0; q < 2; ++q) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&acc_full[q])) : "memory");
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&acc_empty[q])), "r"(kTcRows)
+                         : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&sc_full[q])), "r"(kTcRows)
+                         : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&sc_empty[q])), "r"(kTcRows)
                          : "memory");
         }
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -247,7 +265,6 @@ __global__ void __launch_bounds__(TcCfg<MAXD>::THREADS, 1) k_block_tc(const __gr
         const int grp = p >> 7, row = p & 127;
         for (I i = (I)grp; i < nlocal; i += NGRP) {
             const int st = (int)(i % C::STAGES);
-            const uint32_t use = (uint32_t)(i / C::STAGES);
             const I t = (I)blockIdx.x + i * (I)gridDim.x;
             const I g = t * kTcRows + row;
             const bool valid = g < a.R;
@@ -262,7 +279,18 @@ __global__ void __launch_bounds__(TcCfg<MAXD>::THREADS, 1) k_block_tc(const __gr
             int e = 0;
             frexpf(amax, &e);  // amax <= 2^e
             const float inv = ldexpf(1.0f, -e);
-            if (use >= 1 && !ws_wait(smem_u32(&empty[st]), (use - 1) & 1u, &abort_flag, a.err)) break;
+            // row scale into the ring slot of this tile (the epilogue has read the
+            // scale of tile i - 2 from it)
+            const int es = (int)(i & 1);
+            const uint32_t euse = (uint32_t)(i >> 1);
+            if (euse >= 1 && !ws_wait(smem_u32(&sc_empty[es]), (euse - 1) & 1u, &abort_flag, a.err)) break;
+            erow[es][row] = e;
+            mbar_arrive(smem_u32(&sc_full[es]));
+            if (i >= (I)C::STAGES) {
+                const I w = i - (I)C::STAGES;  // the tile whose MMAs last read this stage
+                if (!ws_wait(smem_u32(&empty[(int)(w % C::NE)]), (uint32_t)(w / C::NE) & 1u, &abort_flag, a.err))
+                    break;
+            }
             unsigned char *X = stages + (uint32_t)st * C::XS * xbytes;
 #pragma unroll
             for (int c0 = 0; c0 < MAXD; c0 += 4) {  // 4 amplitudes = 8 BF16 = one 16-byte chunk per slice
@@ -285,7 +313,6 @@ __global__ void __launch_bounds__(TcCfg<MAXD>::THREADS, 1) k_block_tc(const __gr
                         *reinterpret_cast<uint4 *>(X + (uint32_t)q * xbytes + o) = *reinterpret_cast<const uint4 *>(h[q]);
                 }
             }
-            erow[st][row] = e;
             asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
             mbar_arrive(smem_u32(&full[st]));
         }
@@ -298,7 +325,7 @@ __global__ void __launch_bounds__(TcCfg<MAXD>::THREADS, 1) k_block_tc(const __gr
             // (level, x slice, B slice); the first pair of each level starts its accumulator
             const int pairs[6][3] = {{0, 0, 0}, {1, 0, 1}, {1, 1, 0}, {2, 0, 2}, {2, 1, 1}, {2, 2, 0}};
             const uint32_t ksteps = K / 16u;
-            I issued = 0;
+            I issued = 0, released = 0;
             for (I i = 0; i < nlocal; ++i) {
                 const int st = (int)(i % C::STAGES);
                 if (!ws_wait(smem_u32(&full[st]), (uint32_t)(i / C::STAGES) & 1u, &abort_flag, a.err)) break;
@@ -330,13 +357,22 @@ __global__ void __launch_bounds__(TcCfg<MAXD>::THREADS, 1) k_block_tc(const __gr
                     issued = u + 1;
                 }
                 if (stop) break;
+                mma_commit(smem_u32(&empty[(int)(i % C::NE)]));  // the stage is free once these MMAs complete
+                released = i + 1;
             }
-            // before TMEM is released: the last commit must have completed
+            // before TMEM and the CTA's shared memory are released: the last commits
+            // must have completed
             if (issued > 0) {
                 const I last = issued - 1;
                 const uint32_t mb = smem_u32(&acc_full[last & 1]);
                 for (uint32_t it = 0; it < kWaitLimit; ++it)
                     if (mbar_try(mb, (uint32_t)(last >> 1) & 1u)) break;
+            }
+            if (released > 0) {
+                const I last = released - 1;
+                const uint32_t mb = smem_u32(&empty[(int)(last % C::NE)]);
+                for (uint32_t it = 0; it < kWaitLimit; ++it)
+                    if (mbar_try(mb, (uint32_t)(last / C::NE) & 1u)) break;
             }
         }
     } else {
@@ -344,10 +380,11 @@ __global__ void __launch_bounds__(TcCfg<MAXD>::THREADS, 1) k_block_tc(const __gr
         const int row = tid;         // TMEM lane of this thread (warps 0..3)
         const int Dh = (int)Nh / 2;  // amplitudes per half
         for (I i = 0; i < nlocal; ++i) {
-            const int st = (int)(i % C::STAGES);
-            // the producers' row scales of this stage (phase already complete)
-            if (!ws_wait(smem_u32(&full[st]), (uint32_t)(i / C::STAGES) & 1u, &abort_flag, a.err)) break;
-            const int e = erow[st][row];
+            // the producers' row scale of this tile
+            const int es = (int)(i & 1);
+            if (!ws_wait(smem_u32(&sc_full[es]), (uint32_t)(i >> 1) & 1u, &abort_flag, a.err)) break;
+            const int e = erow[es][row];
+            mbar_arrive(smem_u32(&sc_empty[es]));
             const float escale = ldexpf(1.0f, e);
             const I t = (I)blockIdx.x + i * (I)gridDim.x;
             const I g = t * kTcRows + row;
@@ -395,7 +432,6 @@ __global__ void __launch_bounds__(TcCfg<MAXD>::THREADS, 1) k_block_tc(const __gr
                 mbar_arrive(smem_u32(&acc_empty[sl]));
             }
             if (stop) break;
-            mbar_arrive(smem_u32(&empty[st]));
         }
     }
     __syncthreads();

@@ -134,3 +134,37 @@ def test_tensor_blocks_random(seed):
     for kind in (L.QD_PLAN_GREEDY, L.QD_PLAN_EXHAUSTIVE):
         psi, info = _run(dims, gates, L.QD_C64, kind, psi0=psi0, kmax=3, dmax=64)
         _check(psi, ref, L.QD_C64)
+
+
+@pytest.mark.parametrize("dims", [[4] * 13, [2] * 6 + [3] * 12])
+def test_tensor_blocks_many_tiles_per_cta(dims):
+    """Fused blocks on a register large enough that every CTA of the
+    tensor-core kernel runs tens of tiles, so that each pipeline barrier goes
+    through many phases: the fused complex64 state against the per-gate
+    complex64 state (each already pinned to the oracle) on the device."""
+    rng = np.random.default_rng(31)
+    n = len(dims)
+    gates = []
+    for _ in range(24):
+        qs = [int(x) for x in rng.choice(n, size=3, replace=False)]
+        D = int(np.prod([dims[q] for q in qs]))
+        if D > 64:
+            qs = qs[:2]
+            D = int(np.prod([dims[q] for q in qs]))
+        a, b = qs[0], qs[1]
+        gates.append(wl.Gate("U", (a, b), matrix=wl.haar_unitary(dims[a] * dims[b], rng)))
+        if len(qs) == 3:
+            c = qs[2]
+            gates.append(wl.Gate("U", (b, c), matrix=wl.haar_unitary(dims[b] * dims[c], rng)))
+    with L.Register(dims, None, L.QD_C64) as fused, L.Register(dims, None, L.QD_C64) as ref:
+        plan = L.qd_plan_create(fused.h, gates, L.QD_PLAN_EXHAUSTIVE)
+        classes = {L.kclass_name(int(c)) for c in L.qd_plan_timings(plan, with_times=False)[2]}
+        L.qd_plan_run(plan)
+        assert L.qd_sync(fused.h) == 0
+        L.qd_plan_destroy(plan)
+        L.qd_run_circuit(ref.h, gates, L.QD_PLAN_NONE)
+        assert L.qd_sync(ref.h) == 0
+        ov = L.qd_overlap(ref.h, fused.h)
+        assert abs(ov) ** 2 >= 1 - 1e-6
+        assert abs(L.qd_norm(fused.h) - 1.0) <= 1e-6
+        assert any(c.startswith("tensor_block") for c in classes), classes
