@@ -130,6 +130,7 @@ class ClockSampler:
 
 KERNEL_SOURCES = ("qd_apply.cuh", "qd_common.cuh", "qd_plan.h")
 BATCH_SOURCES = ("qd_batch.cu", "qd_batch.h", "qd_common.cuh")
+TC_SOURCES = ("qd_tc.cu", "qd_tc.h", "qd_common.cuh")
 
 
 def kernel_source_sha(files=KERNEL_SOURCES):
@@ -238,7 +239,8 @@ def run_reference(args, rank, world):
 
 WORKLOAD_C2 = ("8 qubits + 12 ququarts (2^8 * 4^12 = 2^32 amplitudes, 34.4 GB complex64), Haar layer (20) + "
                "d=4 QFT on the ququarts (12 F_4 + 66 controlled phases) + 7 qutrit-style Toffoli rungs (21 CX), "
-               "fused blocks (exhaustive plan) on tcgen05 split-BF16 vs per-gate complex128")
+               "fused complex64 blocks (tcgen05 exact BF16 slices, CUDA-core dense) planned with the learned cost "
+               "model vs per-gate complex128")
 
 
 def run_c2(args, rank, world, local):
@@ -280,21 +282,26 @@ def run_c2(args, rank, world, local):
     res = {}
     reg64 = L.qd_create(dims, None, L.QD_C64, 0, 0, stream.cuda_stream)
     plans = {}
-    for name, kind in (("exhaustive", L.QD_PLAN_EXHAUSTIVE), ("greedy", L.QD_PLAN_GREEDY), ("per_gate", L.QD_PLAN_NONE)):
+    from paper_2211_07918_gb300 import costmodel as cm
+    model = cm.load()
+    L.qd_set_cost_model(reg64, model)
+    for name, kind in (("exhaustive", L.QD_PLAN_EXHAUSTIVE), ("greedy", L.QD_PLAN_GREEDY), ("learned", L.QD_PLAN_LEARNED),
+                       ("per_gate", L.QD_PLAN_NONE)):
         plans[name] = L.qd_plan_create(reg64, gates, kind)
     sampler.start()
-    for name in ("exhaustive", "greedy", "per_gate"):
-        steps = args.steps if name == "exhaustive" else max(2, args.steps // 2)
+    for name in ("exhaustive", "greedy", "learned", "per_gate"):
+        steps = args.steps if name == "learned" else max(2, args.steps // 2)
         ts = timed(reg64, plans[name], steps, min(args.warmup, 3))
         info = L.qd_plan_info(plans[name])
         res[name] = {"ms_per_step": float(np.mean(ts)), "gates_per_s": ngates / (float(np.mean(ts)) * 1e-3),
                      "launches": info["launches"], "blocks": info["blocks"]}
     clocks = sampler.stop()
-    # per-kernel times of the fused plan (per-launch events)
-    L.qd_plan_profile(plans["exhaustive"], True)
+    # per-kernel times of the headline plan: fusion planned with the learned
+    # cost model (per-launch events)
+    L.qd_plan_profile(plans["learned"], True)
     L.qd_reset(reg64)
-    L.qd_plan_run(plans["exhaustive"])
-    ms, ab, kc = L.qd_plan_timings(plans["exhaustive"])
+    L.qd_plan_run(plans["learned"])
+    ms, ab, kc = L.qd_plan_timings(plans["learned"])
     kern = {}
     for t, b_, c in zip(ms, ab, kc):
         k = kern.setdefault(L.kclass_name(int(c)), [0.0, 0.0, 0])
@@ -302,8 +309,9 @@ def run_c2(args, rank, world, local):
         k[1] += float(b_)
         k[2] += 1
     # final fused complex64 state vs the per-gate complex128 state
+    L.qd_plan_profile(plans["learned"], False)
     L.qd_reset(reg64)
-    L.qd_plan_run(plans["exhaustive"])
+    L.qd_plan_run(plans["learned"])
     reg128 = L.qd_create(dims, None, L.QD_C128, 0, 0, stream.cuda_stream)
     plan128 = L.qd_plan_create(reg128, gates, L.QD_PLAN_NONE)
     ts128 = timed(reg128, plan128, max(1, args.steps // 3), 1)
@@ -317,27 +325,31 @@ def run_c2(args, rank, world, local):
     L.qd_plan_destroy(plan128)
     L.qd_destroy(reg64)
     L.qd_destroy(reg128)
+    L.qd_model_destroy(model)
     ms128 = float(np.mean(ts128))
     kname, kdata = max(kern.items(), key=lambda kv: kv[1][0])
     peak, peak_src = measured_peaks()
     achieved = kdata[1] / (kdata[0] * 1e-3) / 1e9
-    value = world * res["exhaustive"]["gates_per_s"]
+    value = world * res["learned"]["gates_per_s"]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": res["exhaustive"]["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": res["learned"]["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD_C2 if args.c2_ququarts == 12 else
                    f"c2 shape with {args.c2_ququarts} ququarts (profiling size)",
+                   "plan": "fusion planned with the learned cost model",
                    "amplitudes": N, "gates": ngates, "precision": "complex64",
                    "l2": "inputs (34.4 GB) larger than L2", "step": "reset + fused circuit"},
         "amp_updates_per_s": value * N,
         "compare": {"fused_exhaustive": res["exhaustive"], "fused_greedy": res["greedy"],
-                    "per_gate_complex64": res["per_gate"],
+                    "fused_learned": res["learned"], "per_gate_complex64": res["per_gate"],
                     "per_gate_complex128": {"ms_per_step": ms128, "gates_per_s": ngates / (ms128 * 1e-3)},
-                    "fused_over_complex128": (ngates / (res["exhaustive"]["ms_per_step"] * 1e-3)) / (ngates / (ms128 * 1e-3)),
+                    "fused_over_complex128": ms128 / res["learned"]["ms_per_step"],
+                    "fused_over_per_gate_complex64": res["per_gate"]["ms_per_step"] / res["learned"]["ms_per_step"],
                     "fidelity_fused_c64_vs_c128": abs(ov) ** 2, "norm2_c64": n64, "norm2_c128": n128},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "kernel": kname, "peak_source": peak_src,
+                     "traffic": profiled_traffic_scaled(kname, kdata[1] / kdata[2], TC_SOURCES),
+                     "kernel": kname, "peak_source": peak_src,
                      "share_of_gate_time": kdata[0] / sum(v[0] for v in kern.values()), "launches": kdata[2]},
         "kernels": {k: {"ms": v[0], "launches": v[2], "GB_s": v[1] / (v[0] * 1e-3) / 1e9} for k, v in kern.items()},
         "clocks": clocks,
