@@ -65,6 +65,54 @@ def dist_env():
     return rank, world, local
 
 
+class Replicas:
+    """One process per GPU, each running an independent replica of the
+    workload (the path has no exchange step): a process group only for the
+    barrier around the timed region and for the maximum of the ranks' times.
+    NCCL with a device, gloo without (the CPU tests)."""
+
+    def __init__(self, world: int, device=None):
+        self.world = world
+        self.dist = None
+        self.device = device
+        if world > 1:
+            import torch.distributed as dist
+            if device is not None and device.type == "cuda":
+                dist.init_process_group("nccl", device_id=device)
+            else:
+                dist.init_process_group("gloo")
+            self.dist = dist
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+        if self.device is not None and self.device.type == "cuda":
+            import torch
+            torch.cuda.synchronize(self.device)
+
+    def max(self, x: float) -> float:
+        """Maximum over ranks (the slowest replica's time)."""
+        if self.dist is None:
+            return float(x)
+        import torch
+        on_gpu = self.device is not None and self.device.type == "cuda"
+        t = torch.tensor([float(x)], dtype=torch.float64, device=self.device if on_gpu else "cpu")
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.dist is not None:
+            self.dist.barrier()
+            self.dist.destroy_process_group()
+            self.dist = None
+
+
+def aggregate_rate(units_per_rank: float, world: int, max_ms: float) -> float:
+    """Whole-job throughput: the units every rank processed over the slowest
+    rank's time."""
+    return world * units_per_rank / (max_ms * 1e-3)
+
+
 # ------------------------------------------------------------------ helpers
 
 def measured_peaks():
@@ -261,12 +309,14 @@ def run_c2(args, rank, world, local):
     N = int(np.prod(dims))
     ngates = len(gates)
     stream = torch.cuda.Stream(device=dev)
+    rep = Replicas(world, dev)
 
     def timed(reg, plan, steps, warmup):
         for _ in range(warmup):
             L.qd_reset(reg)
             L.qd_plan_run(plan)
         stream.synchronize()
+        rep.barrier()
         ts = []
         for _ in range(steps):
             L.qd_reset(reg)
@@ -276,7 +326,8 @@ def run_c2(args, rank, world, local):
             b.record(stream)
             stream.synchronize()
             ts.append(a.elapsed_time(b))
-        return ts
+        rep.barrier()
+        return [rep.max(float(np.mean(ts)))]
 
     sampler = ClockSampler(local)
     res = {}
@@ -330,7 +381,7 @@ def run_c2(args, rank, world, local):
     kname, kdata = max(kern.items(), key=lambda kv: kv[1][0])
     peak, peak_src = measured_peaks()
     achieved = kdata[1] / (kdata[0] * 1e-3) / 1e9
-    value = world * res["learned"]["gates_per_s"]
+    value = aggregate_rate(ngates, world, res["learned"]["ms_per_step"])
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": res["learned"]["ms_per_step"], "higher_is_better": True, "scaling": "weak",
@@ -356,6 +407,7 @@ def run_c2(args, rank, world, local):
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
+    rep.close()
     return 0
 
 
@@ -406,6 +458,7 @@ def run_c3(args, rank, world, local):
     ngates = sum(len(g) for _, g in circuits)
     amp_updates = sum(n * len(g) for n, (_, g) in zip(Ns, circuits))
     stream = torch.cuda.Stream(device=dev)
+    rep = Replicas(world, dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     b = L.qd_batch_create(regs, stream.cuda_stream)
     for c, (_, g) in enumerate(circuits):
@@ -416,6 +469,7 @@ def run_c3(args, rank, world, local):
         for _ in range(warmup):
             run()
         stream.synchronize()
+        rep.barrier()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         for i in range(steps):
             with torch.cuda.stream(stream):
@@ -424,7 +478,8 @@ def run_c3(args, rank, world, local):
             run()
             ev[i][1].record(stream)
         stream.synchronize()
-        return [a.elapsed_time(b_) for a, b_ in ev]
+        rep.barrier()
+        return [rep.max(float(np.mean([a.elapsed_time(b_) for a, b_ in ev])))]
 
     sampler = ClockSampler(local)
     sampler.start()
@@ -485,7 +540,7 @@ def run_c3(args, rank, world, local):
         L.qd_destroy(r)
 
     ms_step = float(np.mean(ms))
-    value = world * ngates / (ms_step * 1e-3)
+    value = aggregate_rate(ngates, world, ms_step)
     peak, peak_src = measured_peaks()
     kmean = float(np.mean(kms))
     achieved = alg_bytes / (kmean * 1e-3) / 1e9
@@ -520,6 +575,7 @@ def run_c3(args, rank, world, local):
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
+    rep.close()
     return 0
 
 
@@ -548,6 +604,7 @@ def run_c4(args, rank, world, local):
     N = int(np.prod(dims))
     ngates = len(gates)
     stream = torch.cuda.Stream(device=dev)
+    rep = Replicas(world, dev)
     model = cm.load()
     reg = L.qd_create(dims, None, L.QD_C64, 0, 0, stream.cuda_stream)
     L.qd_set_cost_model(reg, model)
@@ -557,6 +614,7 @@ def run_c4(args, rank, world, local):
             L.qd_reset(reg)
             L.qd_plan_run(plan)
         stream.synchronize()
+        rep.barrier()
         ts = []
         for _ in range(steps):
             L.qd_reset(reg)
@@ -566,7 +624,8 @@ def run_c4(args, rank, world, local):
             b.record(stream)
             stream.synchronize()
             ts.append(a.elapsed_time(b))
-        return ts
+        rep.barrier()
+        return [rep.max(float(np.mean(ts)))]
 
     res, plans = {}, {}
     for name, kind in (("learned", L.QD_PLAN_LEARNED), ("greedy", L.QD_PLAN_GREEDY),
@@ -611,7 +670,7 @@ def run_c4(args, rank, world, local):
     kname, kdata = max(kern.items(), key=lambda kv: kv[1][0])
     peak, peak_src = measured_peaks()
     achieved = kdata[1] / (kdata[0] * 1e-3) / 1e9
-    value = world * res["learned"]["gates_per_s"]
+    value = aggregate_rate(ngates, world, res["learned"]["ms_per_step"])
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": 1,
         "ms_per_step": res["learned"]["ms_per_step"], "higher_is_better": True, "scaling": "weak",
@@ -631,6 +690,7 @@ def run_c4(args, rank, world, local):
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
+    rep.close()
     return 0
 
 
@@ -645,16 +705,8 @@ def run_ours(args, rank, world, local):
     L.load()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    pg = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
-        pg = dist
-
-    def barrier():
-        if pg is not None:
-            pg.barrier()
-        torch.cuda.synchronize()
+    rep = Replicas(world, dev)
+    barrier = rep.barrier
 
     dims, gates = wl.circuit_c1()
     N = int(np.prod(dims))
@@ -722,13 +774,9 @@ def run_ours(args, rank, world, local):
                        "ms_per_step": float(np.mean(msf)), "launches": nlaunch}
     prof_steps = kern64.pop("_steps")
 
-    total_ms = float(sum(ms64))
-    if pg is not None:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = rep.max(float(sum(ms64)))
     ms_step = total_ms / args.steps
-    value = world * ngates / (ms_step * 1e-3)
+    value = aggregate_rate(ngates, world, ms_step)
     ms_step128 = float(np.mean(ms128))
 
     # dominant kernel class of the c64 path, measured with per-launch events
@@ -819,9 +867,7 @@ def run_ours(args, rank, world, local):
             "wall_s_timed_c64": wall,
         }
         print(json.dumps(line), flush=True)
-    if pg is not None:
-        pg.barrier()
-        pg.destroy_process_group()
+    rep.close()
     return 0
 
 
