@@ -34,8 +34,9 @@
 // (leading byte offset), 8-row groups at K*16 B (stride byte offset).
 //
 // Warp roles (the steps of a tile overlap across tiles):
-//   producers (PW warps, 128 rows per group): gather a tile's groups, slice
-//     them into stage s of a shared-memory ring, arrive full[s];
+//   producers (8 warps: two groups of 128 rows alternating tiles, or above
+//     D = 32 one group with two threads per row): gather a tile's groups,
+//     slice them into stage s of a shared-memory ring, arrive full[s];
 //   MMA issuer (warp 4, one lane): per output half h, wait full[s] and
 //     acc_empty[a], issue the slice products into accumulator slot a of a
 //     2-slot TMEM ring, commit to acc_full[a];
@@ -170,7 +171,12 @@ template <int MAXD> struct TcCfg {
     static constexpr int XS = 3;                        // state slices
     static constexpr int NH = MAXD <= 32 ? 1 : 2;       // output halves
     static constexpr int STAGES = MAXD <= 32 ? 3 : 1;   // shared-memory ring
-    static constexpr int PW = MAXD <= 32 ? 8 : 4;       // producer warps (groups of 128 rows)
+    static constexpr int PW = 8;                        // producer warps
+    // threads per tile row: above 32 amplitudes two threads share a row (32
+    // amplitudes each), so that 8 producer warps fit the registers
+    static constexpr int TPR = MAXD <= 32 ? 1 : 2;
+    static constexpr int NGRP = PW * 32 / (kTcRows * TPR);  // producer groups (alternate tiles)
+    static constexpr int RA = MAXD / TPR;                   // amplitudes per producer thread
     static constexpr int THREADS = 32 * (5 + PW);
     static constexpr int NPAIRS = XS == 3 ? 6 : 5;
     // Stage-release barriers: tile i's MMAs commit to empty[i % NE]; the
@@ -228,7 +234,8 @@ __global__ void __launch_bounds__(TcCfg<MAXD>::THREADS, 1) k_block_tc(const __gr
     }
     if (tid == 0) {
         for (int q = 0; q < C::STAGES; ++q)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&full[q])), "r"(kTcRows) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&full[q])), "r"(kTcRows * C::TPR)
+                         : "memory");
         // a stage is free once the MMAs reading it have completed (tcgen05.commit)
         for (int q = 0; q < C::NE; ++q)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&empty[q])) : "memory");
@@ -260,22 +267,26 @@ __global__ void __launch_bounds__(TcCfg<MAXD>::THREADS, 1) k_block_tc(const __gr
 
     if (warp >= 5) {
         // ------------------------------------------------------------ producers
-        constexpr int NGRP = C::PW / 4;
+        constexpr int NGRP = C::NGRP;
         const int p = tid - 160;
-        const int grp = p >> 7, row = p & 127;
+        const int grp = p / (kTcRows * C::TPR);
+        const int q = p % (kTcRows * C::TPR);
+        const int row = q / C::TPR, part = q % C::TPR;  // this thread's amplitudes: [part RA, (part + 1) RA)
+        const int j0 = part * C::RA;
         for (I i = (I)grp; i < nlocal; i += NGRP) {
             const int st = (int)(i % C::STAGES);
             const I t = (I)blockIdx.x + i * (I)gridDim.x;
             const I g = t * kTcRows + row;
             const bool valid = g < a.R;
             const I base = valid ? expand(g, a.ex) : 0;
-            float2 v[MAXD];
+            float2 v[C::RA];
 #pragma unroll
-            for (int j = 0; j < MAXD; ++j)
-                v[j] = (valid && j < a.D) ? a.psi[base + a.off[j]] : make_float2(0.f, 0.f);
+            for (int j = 0; j < C::RA; ++j)
+                v[j] = (valid && j0 + j < a.D) ? a.psi[base + a.off[j0 + j]] : make_float2(0.f, 0.f);
             float amax = 0.f;
 #pragma unroll
-            for (int j = 0; j < MAXD; ++j) amax = fmaxf(amax, fmaxf(fabsf(v[j].x), fabsf(v[j].y)));
+            for (int j = 0; j < C::RA; ++j) amax = fmaxf(amax, fmaxf(fabsf(v[j].x), fabsf(v[j].y)));
+            if constexpr (C::TPR == 2) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, 1));
             int e = 0;
             frexpf(amax, &e);  // amax <= 2^e
             const float inv = ldexpf(1.0f, -e);
@@ -283,18 +294,25 @@ __global__ void __launch_bounds__(TcCfg<MAXD>::THREADS, 1) k_block_tc(const __gr
             // scale of tile i - 2 from it)
             const int es = (int)(i & 1);
             const uint32_t euse = (uint32_t)(i >> 1);
-            if (euse >= 1 && !ws_wait(smem_u32(&sc_empty[es]), (euse - 1) & 1u, &abort_flag, a.err)) break;
-            erow[es][row] = e;
-            mbar_arrive(smem_u32(&sc_full[es]));
+            // with two threads per row the warp leaves the loop together (the row
+            // maximum is exchanged by shuffles): every lane reaches the vote
+            bool ok = euse < 1 || ws_wait(smem_u32(&sc_empty[es]), (euse - 1) & 1u, &abort_flag, a.err);
+            if constexpr (C::TPR == 2) ok = __all_sync(0xffffffffu, ok);
+            if (!ok) break;
+            if (part == 0) {
+                erow[es][row] = e;
+                mbar_arrive(smem_u32(&sc_full[es]));
+            }
             if (i >= (I)C::STAGES) {
                 const I w = i - (I)C::STAGES;  // the tile whose MMAs last read this stage
-                if (!ws_wait(smem_u32(&empty[(int)(w % C::NE)]), (uint32_t)(w / C::NE) & 1u, &abort_flag, a.err))
-                    break;
+                ok = ws_wait(smem_u32(&empty[(int)(w % C::NE)]), (uint32_t)(w / C::NE) & 1u, &abort_flag, a.err);
             }
+            if constexpr (C::TPR == 2) ok = __all_sync(0xffffffffu, ok);
+            if (!ok) break;
             unsigned char *X = stages + (uint32_t)st * C::XS * xbytes;
 #pragma unroll
-            for (int c0 = 0; c0 < MAXD; c0 += 4) {  // 4 amplitudes = 8 BF16 = one 16-byte chunk per slice
-                if (c0 < a.Dp) {
+            for (int c0 = 0; c0 < C::RA; c0 += 4) {  // 4 amplitudes = 8 BF16 = one 16-byte chunk per slice
+                if (j0 + c0 < a.Dp) {
                     __align__(16) __nv_bfloat16 h[C::XS][8];
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
@@ -307,7 +325,7 @@ __global__ void __launch_bounds__(TcCfg<MAXD>::THREADS, 1) k_block_tc(const __gr
                             h[q][2 * u + 1] = si[q];
                         }
                     }
-                    const uint32_t o = cm_off((uint32_t)row, (uint32_t)(2 * c0), K);
+                    const uint32_t o = cm_off((uint32_t)row, (uint32_t)(2 * (j0 + c0)), K);
 #pragma unroll
                     for (int q = 0; q < C::XS; ++q)
                         *reinterpret_cast<uint4 *>(X + (uint32_t)q * xbytes + o) = *reinterpret_cast<const uint4 *>(h[q]);
