@@ -54,12 +54,13 @@ int qd_debug_fuse_block(const int32_t *dims, int32_t n, const qd_gate *gates, in
  * geometry and work queue exactly as a run does, and replays the queue in
  * order on the host in FP64 with the kernel's index arithmetic, from every
  * register at |0...0>.  amps (2 * total doubles) receives the final states
- * (interleaved complex, arena order); info (5 int64): segments, work items,
+ * (interleaved complex, circuit after circuit); info (5 int64): segments, work items,
  * largest tile, algorithmic bytes, and an error mask: 1 an item waits on a
  * later one, 2 a tile index leaves its register, 4 a segment's tiles do not
  * cover the register exactly once, 8 a gate index leaves its tile, 16 a
  * chunk of gate descriptors overflows its shared-memory area or is
- * misaligned. */
+ * misaligned, 32 a tile gathered as amplitude pairs has a pair that is not
+ * 16-byte aligned in the arena. */
 int qd_debug_batch_emulate(int32_t ncirc, const int32_t *nqudits, const int32_t *dims_concat, const qd_gate *gates,
                            const int32_t *ngates, const int64_t *tune, double *amps, int64_t *info);
 #ifdef __cplusplus

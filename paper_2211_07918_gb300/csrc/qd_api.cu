@@ -1475,7 +1475,8 @@ struct qd_batch {
     std::vector<std::vector<int32_t>> dims;
     std::vector<uint64_t> N, offs, basis;
     std::vector<std::vector<Stored>> circ;
-    uint64_t total = 0;
+    uint64_t total = 0;       // amplitudes of all registers
+    uint64_t arena_amps = 0;  // arena size: every register padded to an even count
     uint32_t tile_amps = 4096;
     int32_t ctas_per_sm = 0;
     uint32_t small_amps = 2048;
@@ -1709,6 +1710,7 @@ int batch_tables(const qd_batch *b, BatchTables &tb) {
             sg.T = (uint32_t)T;
             sg.B = (uint32_t)B;
             sg.divB = make_fastdiv32((uint32_t)B);
+            sg.pair = (B % 2 == 0) ? 1u : 0u;
             sg.hoff = (uint32_t)hoff.size();
             const uint64_t H = T / B;
             {
@@ -1871,9 +1873,10 @@ int batch_shape(qd_batch *b, int32_t ncirc, const int32_t *nqudits, const int32_
         }
         b->dims.push_back(d);
         b->N.push_back(N);
-        b->offs.push_back(b->total);
+        b->offs.push_back(b->arena_amps);
         b->basis.push_back(0);
         b->total += N;
+        b->arena_amps += (N + 1) & ~uint64_t(1);
     }
     b->circ.assign(ncirc, {});
     return QD_OK;
@@ -1882,7 +1885,7 @@ int batch_shape(qd_batch *b, int32_t ncirc, const int32_t *nqudits, const int32_
 BatchLaunch batch_desc(const qd_batch *b) {
     BatchLaunch L;
     L.arena = b->arena;
-    L.total = b->total;
+    L.total = b->arena_amps;
     L.offs = b->doffs;
     L.basis = b->dbasis;
     L.segs = b->dsegs;
@@ -1924,8 +1927,8 @@ int qd_batch_create(int32_t ncirc, const int32_t *nqudits, const int32_t *dims_c
         delete b;
         return cuda_fail(e, "device query");
     }
-    if (cudaMalloc(&b->arena, b->total * sizeof(float2)) != cudaSuccess ||
-        cudaMalloc(&b->probs, b->total * sizeof(double)) != cudaSuccess ||
+    if (cudaMalloc(&b->arena, b->arena_amps * sizeof(float2)) != cudaSuccess ||
+        cudaMalloc(&b->probs, b->arena_amps * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&b->doffs, ncirc * sizeof(uint64_t)) != cudaSuccess ||
         cudaMalloc(&b->dbasis, ncirc * sizeof(uint64_t)) != cudaSuccess ||
         cudaMalloc(&b->dcounters, (ncirc + 1) * sizeof(uint32_t)) != cudaSuccess ||
@@ -2154,7 +2157,7 @@ int qd_debug_batch_emulate(int32_t ncirc, const int32_t *nqudits, const int32_t 
     }
     BatchTables tb;
     if (int rc = batch_tables(&b, tb)) return rc;
-    std::vector<std::complex<double>> psi(b.total);
+    std::vector<std::complex<double>> psi(b.arena_amps);
     for (int c = 0; c < ncirc; ++c) psi[b.offs[c] + b.basis[c]] = 1.0;
     std::vector<uint32_t> done(ncirc, 0);
     std::vector<int> cur_seg(ncirc, -1);
@@ -2187,6 +2190,8 @@ int qd_debug_batch_emulate(int32_t ncirc, const int32_t *nqudits, const int32_t 
             for (uint32_t l = 0; l < S.T; ++l) {
                 const uint32_t h = fdiv(l, S.divB);
                 idx[l] = (uint64_t)base_t + (l - h * S.B) + tb.hoff[S.hoff + h];
+                // paired segments: every even l starts a 16-byte aligned amplitude pair
+                if (S.pair && (l % 2 == 0) && (((b.offs[c] + idx[l]) & 1u) || l + 1 >= S.T)) errors |= 32;
                 if (idx[l] >= N) {
                     errors |= 2;
                     idx[l] = 0;
@@ -2240,10 +2245,12 @@ int qd_debug_batch_emulate(int32_t ncirc, const int32_t *nqudits, const int32_t 
     }
     for (int c = 0; c < ncirc; ++c)
         if (cur_seg[c] >= 0) close_segment(c);
-    for (uint64_t i = 0; i < b.total; ++i) {
-        amps[2 * i] = psi[i].real();
-        amps[2 * i + 1] = psi[i].imag();
-    }
+    uint64_t o = 0;
+    for (int c = 0; c < ncirc; ++c)
+        for (uint64_t i = 0; i < b.N[c]; ++i, ++o) {
+            amps[2 * o] = psi[b.offs[c] + i].real();
+            amps[2 * o + 1] = psi[b.offs[c] + i].imag();
+        }
     info[0] = (int64_t)tb.segs.size();
     info[1] = (int64_t)tb.items.size();
     info[2] = (int64_t)tb.cap;

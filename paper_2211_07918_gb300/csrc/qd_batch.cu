@@ -320,8 +320,15 @@ __device__ __forceinline__ void apply_gate(const BGate &G, float2 *st, const flo
 #undef QD_BATCH_CASE
 }
 
-// Gather (LOAD) or scatter one tile between the state and shared memory, 8
-// independent accesses in flight per thread.
+// State gathers bypass L1 (another CTA may have written the amplitudes).
+__device__ __forceinline__ void cp_async_cg16(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+// Gather (LOAD) or scatter one tile between the state and shared memory.
+// Paired segments gather 16-byte amplitude pairs asynchronously (the caller
+// waits with cp_async_wait_all); otherwise 8 accesses per thread in flight.
 template <bool LOAD>
 __device__ __forceinline__ void move_tile(float2 *psi, float2 *st, const BSeg &S, uint32_t tb,
                                           const uint32_t *__restrict__ hoff) {
@@ -332,6 +339,10 @@ __device__ __forceinline__ void move_tile(float2 *psi, float2 *st, const BSeg &S
         const uint32_t h = fdiv(l, divB);
         return tb + (l - h * B) + __ldg(hoff + h);
     };
+    if (LOAD && S.pair) {
+        for (uint32_t l = 2 * threadIdx.x; l < T; l += 2 * kBThreads) cp_async_cg16(st + l, psi + flat(l));
+        return;
+    }
     for (uint32_t l0 = threadIdx.x; l0 < T; l0 += U * kBThreads) {
         if (LOAD) {
             float2 v[U];
@@ -401,7 +412,7 @@ __global__ void __launch_bounds__(kBThreads, 5)
                         load_chunk(s_ch, gates, coef, desc);
                     }
                     if (c == 0) move_tile<true>(psi, st, S, tb, hoff);
-                    if (fresh) cp_async_wait_all();
+                    if (fresh || (c == 0 && S.pair)) cp_async_wait_all();
                     __syncthreads();
                     // s_ch is read once here, before the first gate's barrier: thread 0
                     // rewrites it for the next chunk after the last gate's barrier

@@ -71,6 +71,9 @@ struct BSeg {
     FastDiv32 divB;
     uint32_t hoff;          // offset of this segment's run table in the run-table arena
     uint32_t ntiles;
+    uint32_t pair;          // B even: every run starts at an even arena index (registers start
+                            // even), so tiles are gathered as 16-byte amplitude pairs
+    uint32_t pad;
     Expand32 ex;            // tile index -> flat base of the tile
 };
 
@@ -87,7 +90,7 @@ struct BItem {
 
 struct BatchLaunch {
     float2 *arena;
-    uint64_t total;
+    uint64_t total;  // arena amplitudes (every register padded to an even count)
     const uint64_t *offs;
     const uint64_t *basis;
     const BSeg *segs;
