@@ -360,16 +360,20 @@ __global__ void __launch_bounds__(TcCfg<MAXD>::THREADS, 1) k_block_tc(const __gr
                     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                     const uint32_t acc = tmem + (uint32_t)sl * 3u * Nh;
                     const uint32_t bhalf = (uint32_t)h * (Nh / 8u) * sbo;  // first output row of this half
-#pragma unroll 1
+                    // the pair table is unrolled into constants; a K step moves both
+                    // operands by 256 bytes, i.e. 16 in the descriptors' address field
+                    // (shared addresses stay below 2^18, so the field does not overflow)
+#pragma unroll
                     for (int pp = 0; pp < C::NPAIRS; ++pp) {
                         const uint32_t dcol = acc + (uint32_t)pairs[pp][0] * Nh;
                         const uint32_t xa = x0 + (uint32_t)pairs[pp][1] * xbytes;
                         const uint32_t bt = b0 + (uint32_t)pairs[pp][2] * bbytes + bhalf;
                         const bool first_of_level = (pp == 0 || pp == 1 || pp == 3);
+                        const uint64_t da = smem_desc(xa, lbo, sbo), db = smem_desc(bt, lbo, sbo);
+                        mma_bf16(dcol, da, db, idesc, first_of_level ? 0u : 1u);
 #pragma unroll 1
-                        for (uint32_t ks = 0; ks < ksteps; ++ks)
-                            mma_bf16(dcol, smem_desc(xa + ks * 256u, lbo, sbo), smem_desc(bt + ks * 256u, lbo, sbo),
-                                     idesc, (first_of_level && ks == 0) ? 0u : 1u);
+                        for (uint32_t ks = 1; ks < ksteps; ++ks)
+                            mma_bf16(dcol, da + (uint64_t)(ks * 16u), db + (uint64_t)(ks * 16u), idesc, 1u);
                     }
                     mma_commit(smem_u32(&acc_full[sl]));
                     issued = u + 1;
