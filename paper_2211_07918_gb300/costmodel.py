@@ -47,9 +47,36 @@ def register_size(dims: Sequence[int]) -> int:
 
 def random_launch(rng: np.random.Generator, dims: Sequence[int], dmax: int = 64):
     """Gates that form one launch: a single permutation/diagonal gate, a
-    single dense gate, or a fused block of two dense gates over 2-3 qudits."""
+    single dense gate, a fused block of two dense gates over 2-3 qudits, or
+    a fused block of 2-4 permutations with phases over 2-3 qudits."""
     n = len(dims)
-    kind = rng.choice(["mono", "dense", "block", "block"])
+    kind = rng.choice(["mono", "dense", "block", "block", "monoblock"])
+    if kind == "monoblock":
+        # fused permutations with phases (shifts, clocks, controlled shifts)
+        # on 2-3 qudits: the product runs on the mono kernel
+        for _ in range(50):
+            k = int(rng.integers(2, 4))
+            qs = [int(x) for x in rng.choice(n, size=k, replace=False)]
+            if int(np.prod([dims[q] for q in qs])) <= 32:
+                break
+        else:
+            qs = [0, 1]
+        out = []
+        for _ in range(int(rng.integers(2, 5))):
+            t = int(rng.choice(qs))
+            others = [q for q in qs if q != t]
+            sub = rng.integers(0, 3)
+            if sub == 0:
+                out.append(Gate("X", (t,), param=int(rng.integers(1, dims[t]))))
+            elif sub == 1:
+                out.append(Gate("Z", (t,), param=1))
+            else:
+                c = int(rng.choice(others))
+                out.append(Gate("X", (t,), (c,), (int(rng.integers(0, dims[c])),), int(rng.integers(1, dims[t]))))
+        if len({q for g in out for q in (tuple(g.targets) + tuple(g.controls or ()))}) < 2:
+            c = [q for q in qs if q != out[0].targets[0]][0]
+            out.append(Gate("Z", (c,), param=1))
+        return out
     if kind == "mono":
         q = int(rng.integers(0, n))
         sub = rng.integers(0, 3)

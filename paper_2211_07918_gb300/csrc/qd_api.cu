@@ -946,9 +946,11 @@ int build_plan(qd_reg *r, const std::vector<FuseGate> &fg, const std::vector<con
             if (rc == QD_OK && noop) continue;
         } else {
             FuseBlock b = build_block(fg, sg.first, sg.second, r->dims);
+            bool all_mono = true;  // the product is then a permutation with phases (mono kernel)
+            for (int i = sg.first; i <= sg.second; ++i) all_mono = all_mono && fg[i].mono;
             if ((int)b.qudits.size() > QD_MAX_TARGETS) {
                 rc = fail(QD_ERR_DIM, "fused block spans more than 6 qudits");
-            } else if (r->prec == QD_C64 && b.D >= kTcMinD && b.D <= kTcMaxD) {
+            } else if (r->prec == QD_C64 && b.D >= kTcMinD && b.D <= kTcMaxD && !(all_mono && b.D <= kMonoBlockMaxD)) {
                 tc_terms.emplace_back();
                 rc = plan_block_tc(r, b, g, tc_terms.back());
                 tc_index.push_back((int)p->gates.size());

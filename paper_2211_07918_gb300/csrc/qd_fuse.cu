@@ -186,7 +186,12 @@ double segment_cost(const std::vector<FuseGate> &gates, int first, int last, con
         return cost(launch_features(reg, g.acting, Dt, g.mono ? kKernelMono : kKernelDense, frac));
     }
     const std::vector<int> s = union_qudits(gates, first, last);
-    return cost(launch_features(reg, s, (int)dim_of(s, reg.dims), kKernelBlock, 1.0));
+    const int D = (int)dim_of(s, reg.dims);
+    // a product of permutations with phases is one: it runs on the mono
+    // kernel (up to its 32 local states), not as a dense block
+    bool all_mono = true;
+    for (int i = first; i <= last; ++i) all_mono = all_mono && gates[i].mono;
+    return cost(launch_features(reg, s, D, all_mono && D <= kMonoBlockMaxD ? kKernelMono : kKernelBlock, 1.0));
 }
 
 namespace {

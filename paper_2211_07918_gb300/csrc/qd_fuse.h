@@ -50,6 +50,7 @@ struct RegisterShape {
 constexpr int kKernelMono = 0;   // per-gate permutation with phases
 constexpr int kKernelDense = 1;  // per-gate dense (CUDA cores)
 constexpr int kKernelBlock = 2;  // fused block (tensor cores for complex64, D >= 9)
+constexpr int kMonoBlockMaxD = 32;  // a fused block of permutations with phases up to this D runs as mono
 
 // Feature vector of a launch acting on `qudits` with target dimension D:
 // log2 D, qudit count, log2 of the (up to three) smallest strides, relative

@@ -168,3 +168,30 @@ def test_tensor_blocks_many_tiles_per_cta(dims):
         assert abs(ov) ** 2 >= 1 - 1e-6
         assert abs(L.qd_norm(fused.h) - 1.0) <= 1e-6
         assert any(c.startswith("tensor_block") for c in classes), classes
+
+
+@pytest.mark.parametrize("kind", [L.QD_PLAN_GREEDY, L.QD_PLAN_EXHAUSTIVE])
+def test_fused_permutation_blocks_run_as_mono(kind):
+    """A fused block of permutations with phases (shifts, clocks, controlled
+    shifts) is itself one: in complex64 it runs on the mono kernel, also at
+    D >= 9 where a dense block would go to the tensor cores."""
+    rng = np.random.default_rng(404)
+    dims = [3, 3, 2, 3, 3, 2, 3]
+    gates = []
+    for _ in range(60):
+        t = int(rng.integers(0, len(dims)))
+        sub = int(rng.integers(0, 3))
+        if sub == 0:
+            gates.append(wl.Gate("X", (t,), param=int(rng.integers(1, dims[t]))))
+        elif sub == 1:
+            gates.append(wl.Gate("Z", (t,), param=1))
+        else:
+            c = int(rng.choice([q for q in range(len(dims)) if q != t]))
+            gates.append(wl.Gate("X", (t,), (c,), (int(rng.integers(0, dims[c])),), int(rng.integers(1, dims[t]))))
+    ref = qf.run_circuit(dims, gates)
+    psi, info = _run(dims, gates, L.QD_C64, kind)
+    _check(psi, ref, L.QD_C64)
+    assert info["blocks"] > 0
+    classes = _kclasses(dims, gates, L.QD_C64, kind)
+    assert not any(c.startswith("tensor_block") for c in classes), classes
+    assert any(c.startswith("mono") and int(c.split("_D")[1]) >= 9 for c in classes), classes
