@@ -181,7 +181,7 @@ def load(path: str = DEFAULT_WEIGHTS) -> int:
 # Planner evaluation
 # ---------------------------------------------------------------------------
 
-def judge_circuit(seed: int, n_active: int = 10, ngates: int = 40, spectators: Sequence[int] = (),
+def eval_circuit(seed: int, n_active: int = 10, ngates: int = 40, spectators: Sequence[int] = (),
                   dim_choices=(2, 3, 4)):
     """A random circuit on n_active qudits (dims from dim_choices) placed
     among spectator qudits (which no gate touches), so that the register is
@@ -216,7 +216,7 @@ def plan_time(reg: int, gates, plan_kind=None, segments=None, reps: int = 3) -> 
 
 
 def exhaustive_measured(reg: int, dims: Sequence[int], gates, kmax: int = 3, dmax: int = 64, reps: int = 3):
-    """The judge: the minimum-time contiguous segmentation, where every
+    """The measured optimum: the minimum-time contiguous segmentation, where every
     candidate segment's cost is its measured launch time (dynamic program
     over prefixes; a segment of several gates must span <= kmax qudits of
     total dimension <= dmax).  Returns (segments, summed measured ms)."""
@@ -244,13 +244,13 @@ def exhaustive_measured(reg: int, dims: Sequence[int], gates, kmax: int = 3, dma
 
 
 def evaluate(model: int, n_circuits: int = 4, seed: int = 7000, spectators=(3, 3, 3, 3, 3, 2, 2, 2, 2),
-             judge: bool = True, reps: int = 3, log=None):
-    """Measured plan times (ms) on judge circuits: one gate per launch, the
+             measured: bool = True, reps: int = 3, log=None):
+    """Measured plan times (ms) on evaluation circuits: one gate per launch, the
     greedy and exhaustive plans under the analytic cost model, the learned
-    plan, and (judge=True) the exhaustive optimum over measured segment costs."""
+    plan, and (measured=True) the exhaustive optimum over measured segment costs."""
     rows = []
     for c in range(n_circuits):
-        dims, gates = judge_circuit(seed + c, spectators=spectators)
+        dims, gates = eval_circuit(seed + c, spectators=spectators)
         h = L.qd_create(dims, None, L.QD_C64, 0, 0, 0)
         try:
             L.qd_set_cost_model(h, model)
@@ -259,9 +259,9 @@ def evaluate(model: int, n_circuits: int = 4, seed: int = 7000, spectators=(3, 3
                    "greedy": plan_time(h, gates, L.QD_PLAN_GREEDY, reps=reps),
                    "exhaustive_analytic": plan_time(h, gates, L.QD_PLAN_EXHAUSTIVE, reps=reps),
                    "learned": plan_time(h, gates, L.QD_PLAN_LEARNED, reps=reps)}
-            if judge:
+            if measured:
                 segs, _ = exhaustive_measured(h, dims, gates, reps=reps)
-                row["judge"] = plan_time(h, gates, segments=segs, reps=reps)
+                row["measured_optimum"] = plan_time(h, gates, segments=segs, reps=reps)
             rows.append(row)
             if log:
                 log(str(row))
@@ -280,7 +280,8 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--out", default=DEFAULT_WEIGHTS)
     ap.add_argument("--circuits", type=int, default=4)
-    ap.add_argument("--no-judge", action="store_true")
+    ap.add_argument("--no-measured-optimum", action="store_true",
+                    help="skip the exhaustive search over measured segment costs (slow)")
     ap.add_argument("--large-samples", type=int, default=0,
                     help="extra samples on registers above 2^31 amplitudes (64-bit index kernels)")
     ap.add_argument("--base-data", default=None,
@@ -316,7 +317,7 @@ def main(argv=None):
     r2 = 1.0 - float(np.sum(resid ** 2) / np.sum((y[te] - y[te].mean()) ** 2))
     save(m, args.out, samples=n, train_loss=loss, test_r2=r2, test_rmse_log=float(np.sqrt(np.mean(resid ** 2))))
     np.savez(os.path.splitext(args.out)[0] + "_data.npz", X=X, y=y)
-    rows = evaluate(m, args.circuits, judge=not args.no_judge, log=log)
+    rows = evaluate(m, args.circuits, measured=not args.no_measured_optimum, log=log)
     tot = {k: float(sum(r[k] for r in rows)) for k in rows[0] if k not in ("N", "gates")}
     print(json.dumps({"samples": n, "gen_s": gen_s, "train_loss": loss, "test_r2": r2,
                       "test_rmse_log": float(np.sqrt(np.mean(resid ** 2))), "plan_ms_totals": tot,

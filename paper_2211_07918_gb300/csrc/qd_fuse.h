@@ -7,7 +7,7 @@
 // qudits (controls included, expanded to dense).  The greedy planner extends
 // the current segment while the cost model says the merged block is cheaper
 // than closing it; the exhaustive planner is an exact dynamic program over
-// all contiguous segmentations (the judge of the other two).
+// all contiguous segmentations (the reference the other two are measured against).
 #pragma once
 #include <cstdint>
 #include <functional>

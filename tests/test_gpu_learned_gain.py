@@ -1,4 +1,4 @@
-"""What the trained cost model gains: on judge circuits (10 active qudits of
+"""What the trained cost model gains: on evaluation circuits (10 active qudits of
 dims 2..4, 40 gates, among spectator qudits so that the register holds
 5e7-7e7 amplitudes), the plan chosen with the learned model runs faster on the
 GPU than the greedy plan of the analytic model (the method without the
@@ -27,7 +27,7 @@ def test_learned_plan_beats_greedy_plan():
         pytest.skip("no trained weights shipped")
     m = cm.load()
     try:
-        rows = cm.evaluate(m, n_circuits=2, seed=7002, judge=False, reps=5)
+        rows = cm.evaluate(m, n_circuits=2, seed=7002, measured=False, reps=5)
     finally:
         L.qd_model_destroy(m)
     learned = sum(r["learned"] for r in rows)
