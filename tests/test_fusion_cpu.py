@@ -113,3 +113,20 @@ def test_identity_gates_are_dropped_before_fusion():
     gates = [Gate("H", (0,)), Gate("Z", (1,), param=3), Gate("H", (1,))]
     segs, _ = L.qd_debug_fuse_plan(dims, gates, L.QD_PLAN_NONE)
     assert len(segs) == 2
+
+
+def test_segment_of_permutations_is_costed_as_mono():
+    """A fused segment whose gates are all permutations with phases is itself
+    one and runs on the mono kernel: the cost model sees a memory-only launch.
+    In complex128, where a dense 9 x 9 block is arithmetic-bound, the fused
+    [X, CX] segment therefore costs less than the fused [H, CX] one on the
+    same two qutrits, and no more than the single-qutrit permutation alone
+    (the same pass over the state)."""
+    dims = [3] * 16
+    mono = [Gate("X", (4,), param=1), Gate("X", (9,), (4,), (2,), 2)]
+    dense = [Gate("H", (4,)), Gate("X", (9,), (4,), (2,), 2)]
+    c_mono = L.qd_debug_segment_cost(dims, mono, 0, 1, L.QD_C128)
+    c_dense = L.qd_debug_segment_cost(dims, dense, 0, 1, L.QD_C128)
+    c_single = L.qd_debug_segment_cost(dims, mono, 0, 0, L.QD_C128)
+    assert c_mono < c_dense
+    assert c_mono <= c_single * 1.0001
