@@ -169,7 +169,11 @@ __device__ __forceinline__ void slices(float v, __nv_bfloat16 *out) {
 // random +-2^-18/sqrt(N) per block, visible on small registers.)
 template <int MAXD> struct TcCfg {
     static constexpr int XS = 3;                        // state slices
-    static constexpr int NH = MAXD <= 32 ? 1 : 2;       // output halves
+    static constexpr int NH = 1;                        // output parts (N = 2 Dp in one MMA pass)
+    // TMEM accumulator slots (3 levels x N columns each, 512 columns per SM):
+    // two above D = 32 would not fit, so there the next tile's MMAs wait for
+    // the epilogue to drain the single slot
+    static constexpr int SLOTS = MAXD <= 32 ? 2 : 1;
     static constexpr int STAGES = MAXD <= 32 ? 3 : 1;   // shared-memory ring
     static constexpr int PW = 8;                        // producer warps
     // threads per tile row: above 32 amplitudes two threads share a row (32
@@ -224,7 +228,7 @@ __global__ void __launch_bounds__(TcCfg<MAXD>::THREADS, 1) k_block_tc(const __gr
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
     uint32_t ncols = 32;
-    while (ncols < 2u * 3u * Nh) ncols <<= 1;
+    while (ncols < (uint32_t)C::SLOTS * 3u * Nh) ncols <<= 1;
 
     {
         const uint4 *src = reinterpret_cast<const uint4 *>(a.terms);
@@ -351,9 +355,9 @@ __global__ void __launch_bounds__(TcCfg<MAXD>::THREADS, 1) k_block_tc(const __gr
                 bool stop = false;
                 for (int h = 0; h < C::NH; ++h) {
                     const I u = i * C::NH + h;
-                    const int sl = (int)(u & 1);
-                    if (u >= 2 &&
-                        !ws_wait(smem_u32(&acc_empty[sl]), (uint32_t)((u >> 1) - 1) & 1u, &abort_flag, a.err)) {
+                    const int sl = (int)(u % C::SLOTS);
+                    if (u >= (I)C::SLOTS && !ws_wait(smem_u32(&acc_empty[sl]), (uint32_t)(u / C::SLOTS - 1) & 1u,
+                                                       &abort_flag, a.err)) {
                         stop = true;
                         break;
                     }
@@ -386,9 +390,9 @@ __global__ void __launch_bounds__(TcCfg<MAXD>::THREADS, 1) k_block_tc(const __gr
             // must have completed
             if (issued > 0) {
                 const I last = issued - 1;
-                const uint32_t mb = smem_u32(&acc_full[last & 1]);
+                const uint32_t mb = smem_u32(&acc_full[(int)(last % C::SLOTS)]);
                 for (uint32_t it = 0; it < kWaitLimit; ++it)
-                    if (mbar_try(mb, (uint32_t)(last >> 1) & 1u)) break;
+                    if (mbar_try(mb, (uint32_t)(last / C::SLOTS) & 1u)) break;
             }
             if (released > 0) {
                 const I last = released - 1;
@@ -415,8 +419,8 @@ __global__ void __launch_bounds__(TcCfg<MAXD>::THREADS, 1) k_block_tc(const __gr
             bool stop = false;
             for (int h = 0; h < C::NH; ++h) {
                 const I u = i * C::NH + h;
-                const int sl = (int)(u & 1);
-                if (!ws_wait(smem_u32(&acc_full[sl]), (uint32_t)(u >> 1) & 1u, &abort_flag, a.err)) {
+                const int sl = (int)(u % C::SLOTS);
+                if (!ws_wait(smem_u32(&acc_full[sl]), (uint32_t)(u / C::SLOTS) & 1u, &abort_flag, a.err)) {
                     stop = true;
                     break;
                 }
@@ -549,9 +553,9 @@ static cudaError_t launch_tc_im(const GatePlan &g, void *psi, int sm_count, int3
     if (e != cudaSuccess) return e;
     int occ = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, C::THREADS, smem);
-    // TMEM: 512 columns per SM; each CTA holds the next power of two >= 2 slots * 3 levels * N/NH
+    // TMEM: 512 columns per SM; each CTA holds the next power of two >= slots * 3 levels * N/NH
     int ncols = 32;
-    while (ncols < 2 * 3 * 2 * g.Dp / C::NH) ncols <<= 1;
+    while (ncols < C::SLOTS * 3 * 2 * g.Dp / C::NH) ncols <<= 1;
     const int tmem_cap = 512 / ncols;
     occ = occ < 1 ? 1 : (occ > tmem_cap ? tmem_cap : occ);
     const uint64_t tiles = (g.R + kTcRows - 1) / kTcRows;
