@@ -3,8 +3,12 @@
 A multilayer perceptron 12 -> 64 -> 64 -> 64 -> 1 with ReLU hidden units and
 a mean-squared-error loss, written out with numpy in FP64, with the same flat
 parameter layout as the library: W1 (12x64, row = input), b1, W2 (64x64), b2,
-W3 (64x64), b3, W4 (64), b4.  Gradients by the chain rule; pinned in the tests
-by central finite differences.  The paper has no learned component; this is
+W3 (64x64), b3, W4 (64), b4.  Gradients by the chain rule.  Pinned in the
+tests without going through this module's own arithmetic: the forward pass by
+a hand-set network whose output is written down in closed form (with a
+negative pre-activation on every layer that must clip) and by a per-neuron
+scalar loop; the gradients by central finite differences of that pinned
+forward pass.  The paper has no learned component; this is
 the checker of the library's own forward and backward kernels.
 """
 from __future__ import annotations
