@@ -47,14 +47,20 @@ def parse():
                     help="ququarts of the c2 register (12: the full 2^32-amplitude case; fewer for profiling)")
     ap.add_argument("--c3-circuits", type=int, default=256,
                     help="circuits of the c3 batch (256: the full workload; fewer for profiling)")
-    ap.add_argument("--workload", default="c1", choices=["c1", "c2", "c3", "c4"],
-                    help="c1: 14 qutrits, 500 gates, per-gate kernels (default); "
-                         "c2: 8 qubits + 12 ququarts (2^32 amplitudes), Haar layer + d=4 QFT + Toffoli ladder, "
-                         "fused tensor-core blocks vs the FP64 per-gate path; "
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "strides", "blocks"],
+                    help="c2 (default): 8 qubits + 12 ququarts (2^32 amplitudes), Haar layer + d=4 QFT + Toffoli "
+                         "ladder, fused complex64 plan (learned cost model) vs the FP64 per-gate path; "
+                         "c1: 14 qutrits, 500 gates, per-gate kernels; "
                          "c3: 256 independent circuits (6-12 qudits, dims 2..5, 200 gates each) in one persistent "
                          "graph-captured launch vs one graph-captured plan per circuit; "
                          "c4: 18 qutrits + 4 qubits (6.2e9 amplitudes), 1,000-gate circuit, fusion planned with "
-                         "the learned cost model vs the greedy and exhaustive analytic plans and per-gate kernels")
+                         "the learned cost model vs the greedy and exhaustive analytic plans and per-gate kernels; "
+                         "strides: per-gate kernels on every target position of the c4 register (per-stride table); "
+                         "blocks: fused blocks of D 6..64 on the tensor cores and on the CUDA-core dense kernels")
+    ap.add_argument("--blocks-small", action="store_true",
+                    help="blocks workload on a 2^26-amplitude register (8 qubits + 9 ququarts) only: the profiling size")
+    ap.add_argument("--strides-register", default="c4", choices=["c4", "c2"],
+                    help="register of the per-stride table (c4: 3^18 * 2^4; c2: 2^8 * 4^12)")
     return ap.parse_args()
 
 
@@ -258,46 +264,128 @@ def cpu_baseline_obj(dims, gates, ngates, min_seconds=10.0, max_reps=20):
 # --------------------------------------------------------------- reference
 
 def run_reference(args, rank, world):
+    """The reference arm: the FP64 C oracle on the host cores, on this bench's
+    workload (the 2^32-amplitude QFT + Toffoli-ladder circuit), each step a
+    bounded sample: the sample gates applied to a same-shaped 2^24-amplitude
+    register, the amplitude-update rate scaled to gates/s of the full
+    register.  Under torchrun only rank 0 runs it."""
     if rank != 0:
         return 0
+    from oracle import fast as qf
+    from oracle import qudit_oracle as qo
     from paper_2211_07918_gb300 import workloads as wl
-    dims, gates = wl.circuit_c1()
-    n = args.cpu_sample_gates or 100
+    dims, gates = wl.circuit_c2()
+    small = [2] * 8 + [4] * 8
+    sub = c2_cpu_sample(gates, len(small))
+    qf.build()
+    psi = qo.basis_state(small)
     for _ in range(args.warmup):
-        cpu_sample(dims, gates, 1)
-    rates, cores, secs = [], 0, 0.0
+        qf.apply(psi, small, sub[0])
+    secs = 0.0
     for _ in range(args.steps):
-        r, cores, dt = cpu_sample(dims, gates, n)
-        rates.append(r)
-        secs += dt
-    value = float(len(rates) * n / secs)
+        t0 = time.perf_counter()
+        for g in sub:
+            qf.apply(psi, small, g)
+        secs += time.perf_counter() - t0
+    upd = args.steps * len(sub) * int(np.prod(small)) / secs
+    value = upd / int(np.prod(dims))
+    sample = (f"per step the {len(sub)} sample gates of the circuit (every gate acting below qudit 16, evenly "
+              f"spread) on a 2^8 * 4^8 register (2^24 amplitudes), FP64 C index loop (OpenMP); "
+              f"{upd:.3g} amplitude updates/s extrapolated to 2^32")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": WORKLOAD + "; each step times a bounded sample of the circuit",
-                       "sample_gates_per_step": n},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"first {n} gates of the 500-gate circuit per step, full register"},
+            "config": {"workload": WORKLOAD_C2 + "; each step times a bounded sample of the circuit",
+                       "amplitudes": int(np.prod(dims)), "gates": len(gates), "sample_gates_per_step": len(sub)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": qf.max_threads(), "kind": "oracle",
+                             "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def c2_cpu_sample(gates, nq_small, count=10):
+    """``count`` gates spread evenly over the circuit among those acting only
+    on qudits below nq_small (so that they apply to the smaller register)."""
+    ok = [g for g in gates if max(tuple(g.targets) + tuple(g.controls or ())) < nq_small]
+    idx = np.linspace(0, len(ok) - 1, min(count, len(ok))).round().astype(int)
+    return [ok[i] for i in idx]
 
 
 # -------------------------------------------------------------------- ours
 
 WORKLOAD_C2 = ("8 qubits + 12 ququarts (2^8 * 4^12 = 2^32 amplitudes, 34.4 GB complex64), Haar layer (20) + "
                "d=4 QFT on the ququarts (12 F_4 + 66 controlled phases) + 7 qutrit-style Toffoli rungs (21 CX), "
-               "fused complex64 blocks (tcgen05 exact BF16 slices, CUDA-core dense) planned with the learned cost "
-               "model vs per-gate complex128")
+               "fused complex64 plan chosen with the learned cost model (tcgen05 exact-BF16-slice blocks, "
+               "CUDA-core blocks, diagonal-run tables) vs per-gate complex128")
+
+
+def cpu_baseline_c2(dims, gates, min_seconds=10.0, prefix=10):
+    """The FP64 C oracle (index loop, OpenMP over the host cores) on
+    ``prefix`` gates spread over the circuit, on a register of the same shape
+    with 8 ququarts instead of 12 (2^24 amplitudes; the full state would need
+    68.7 GB in complex128), repeated until ``min_seconds`` have run.  The
+    measured amplitude-update rate is scaled to gates/s of the full 2^32
+    register."""
+    from oracle import fast as qf
+    from oracle import qudit_oracle as qo
+    qf.build()
+    small = [2] * 8 + [4] * 8
+    sub = c2_cpu_sample(gates, len(small), prefix)
+    psi = qo.basis_state(small)
+    secs, done = 0.0, 0
+    while secs < min_seconds:
+        t0 = time.perf_counter()
+        for g in sub:
+            qf.apply(psi, small, g)
+        secs += time.perf_counter() - t0
+        done += len(sub)
+    n_small = int(np.prod(small))
+    upd_per_s = done * n_small / secs
+    return {"value": upd_per_s / int(np.prod(dims)), "unit": UNIT, "cores": qf.max_threads(), "kind": "oracle",
+            "sample": f"{done // len(sub)} x {len(sub)} gates spread over the circuit on a 2^8 * 4^8 register "
+                      f"(same shape, 2^24 amplitudes), FP64 C index loop (OpenMP), {secs:.1f} s; "
+                      f"{upd_per_s:.3g} amplitude updates/s extrapolated to the 2^32 register",
+            "amp_updates_per_s": upd_per_s, "extrapolated": True}
+
+
+def c1_summary(L, stream, steps: int):
+    """The 14-qutrit per-gate workload (4.78e6 amplitudes, L2-resident) in
+    complex64 and complex128, graph replay, for the compare block."""
+    import torch
+    from paper_2211_07918_gb300 import workloads as wl
+    dims, gates = wl.circuit_c1()
+    out = {}
+    for name, prec in (("complex64", L.QD_C64), ("complex128", L.QD_C128)):
+        reg = L.qd_create(dims, None, prec, 0, 0, stream.cuda_stream)
+        plan = L.qd_plan_create(reg, gates, L.QD_PLAN_NONE)
+        for _ in range(3):
+            L.qd_reset(reg)
+            L.qd_plan_run(plan)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for a, b in ev:
+            a.record(stream)
+            L.qd_reset(reg)
+            L.qd_plan_run(plan)
+            b.record(stream)
+        stream.synchronize()
+        ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+        out[name] = {"ms_per_step": ms, "gates_per_s": len(gates) / (ms * 1e-3)}
+        L.qd_plan_destroy(plan)
+        L.qd_destroy(reg)
+    out["workload"] = "14 qutrits (3^14 amplitudes, L2-resident), 500 gates, per-gate kernels, reset + circuit"
+    return out
 
 
 def run_c2(args, rank, world, local):
-    """Precision and fusion at scale: the fused complex64 path (blocks of up to
-    3 qudits, D <= 64, on the tensor cores) against the plain per-gate
-    complex128 path on the same GPU; fidelity through qd_overlap on the device."""
+    """Precision and fusion at scale (the metric's configuration): the fused
+    complex64 path, planned with the learned cost model, against the plain
+    per-gate complex128 path on the same GPU; fidelity through qd_overlap on
+    the device; end to end through the C ABI with host buffers."""
     import torch
 
+    from paper_2211_07918_gb300 import costmodel as cm
     from paper_2211_07918_gb300 import qudit as L
     from paper_2211_07918_gb300 import workloads as wl
     from paper_2211_07918_gb300.build import build
@@ -309,102 +397,147 @@ def run_c2(args, rank, world, local):
     dims, gates = wl.circuit_c2(n_ququarts=args.c2_ququarts)
     N = int(np.prod(dims))
     ngates = len(gates)
+    full = args.c2_ququarts == 12
     stream = torch.cuda.Stream(device=dev)
     rep = Replicas(world, dev)
 
     def timed(reg, plan, steps, warmup):
+        """Per-step CUDA events on the register's stream: reset + plan."""
         for _ in range(warmup):
             L.qd_reset(reg)
             L.qd_plan_run(plan)
         stream.synchronize()
         rep.barrier()
-        ts = []
-        for _ in range(steps):
-            L.qd_reset(reg)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for a, b in ev:
             a.record(stream)
+            L.qd_reset(reg)
             L.qd_plan_run(plan)
             b.record(stream)
-            stream.synchronize()
-            ts.append(a.elapsed_time(b))
+        stream.synchronize()
         rep.barrier()
-        return [rep.max(float(np.mean(ts)))]
+        return rep.max(float(np.mean([a.elapsed_time(b) for a, b in ev])))
 
-    sampler = ClockSampler(local)
-    res = {}
     reg64 = L.qd_create(dims, None, L.QD_C64, 0, 0, stream.cuda_stream)
-    plans = {}
-    from paper_2211_07918_gb300 import costmodel as cm
     model = cm.load()
     L.qd_set_cost_model(reg64, model)
-    for name, kind in (("exhaustive", L.QD_PLAN_EXHAUSTIVE), ("greedy", L.QD_PLAN_GREEDY), ("learned", L.QD_PLAN_LEARNED),
-                       ("per_gate", L.QD_PLAN_NONE)):
+    plans, res = {}, {}
+    for name, kind in (("learned", L.QD_PLAN_LEARNED), ("exhaustive_analytic", L.QD_PLAN_EXHAUSTIVE),
+                       ("greedy_analytic", L.QD_PLAN_GREEDY), ("per_gate", L.QD_PLAN_NONE)):
+        t0 = time.perf_counter()
         plans[name] = L.qd_plan_create(reg64, gates, kind)
+        res[name] = {"plan_s": time.perf_counter() - t0}
+    sampler = ClockSampler(local)
     sampler.start()
-    for name in ("exhaustive", "greedy", "learned", "per_gate"):
-        steps = args.steps if name == "learned" else max(2, args.steps // 2)
-        ts = timed(reg64, plans[name], steps, min(args.warmup, 3))
-        info = L.qd_plan_info(plans[name])
-        res[name] = {"ms_per_step": float(np.mean(ts)), "gates_per_s": ngates / (float(np.mean(ts)) * 1e-3),
-                     "launches": info["launches"], "blocks": info["blocks"]}
+    ms = timed(reg64, plans["learned"], args.steps, args.warmup)
     clocks = sampler.stop()
-    # per-kernel times of the headline plan: fusion planned with the learned
-    # cost model (per-launch events)
+    res["learned"].update({"ms_per_step": ms, "gates_per_s": ngates / (ms * 1e-3)})
+    for name in ("exhaustive_analytic", "greedy_analytic", "per_gate"):
+        t = timed(reg64, plans[name], max(2, args.steps // 4), 2)
+        res[name].update({"ms_per_step": t, "gates_per_s": ngates / (t * 1e-3)})
+    for name, p_ in plans.items():
+        info = L.qd_plan_info(p_)
+        res[name].update({"launches": info["launches"], "blocks": info["blocks"]})
+    # per-kernel times of the headline plan (per-launch events, direct launches)
     L.qd_plan_profile(plans["learned"], True)
-    L.qd_reset(reg64)
-    L.qd_plan_run(plans["learned"])
-    ms, ab, kc = L.qd_plan_timings(plans["learned"])
-    kern = {}
-    for t, b_, c in zip(ms, ab, kc):
+    kern, launch_list = {}, []
+    for _ in range(2):
+        L.qd_reset(reg64)
+        L.qd_plan_run(plans["learned"])
+        ms_l, ab_l, kc_l = L.qd_plan_timings(plans["learned"])
+    for t, b_, c in zip(ms_l, ab_l, kc_l):
         k = kern.setdefault(L.kclass_name(int(c)), [0.0, 0.0, 0])
         k[0] += float(t)
         k[1] += float(b_)
         k[2] += 1
-    # final fused complex64 state vs the per-gate complex128 state
+        launch_list.append([L.kclass_name(int(c)), round(float(t), 3), round(float(b_) / (float(t) * 1e6), 1)])
     L.qd_plan_profile(plans["learned"], False)
+    alg_bytes_step = float(np.sum(ab_l))
+    # fused complex64 state vs the plain per-gate complex128 state
     L.qd_reset(reg64)
     L.qd_plan_run(plans["learned"])
     reg128 = L.qd_create(dims, None, L.QD_C128, 0, 0, stream.cuda_stream)
     plan128 = L.qd_plan_create(reg128, gates, L.QD_PLAN_NONE)
-    ts128 = timed(reg128, plan128, max(1, args.steps // 3), 1)
+    ms128 = timed(reg128, plan128, max(1, args.steps // 10), 1)
     L.qd_reset(reg128)
     L.qd_plan_run(plan128)
     ov = L.qd_overlap(reg128, reg64)
-    n64 = L.qd_norm(reg64)
-    n128 = L.qd_norm(reg128)
-    for p_ in plans.values():
-        L.qd_plan_destroy(p_)
+    n64, n128 = L.qd_norm(reg64), L.qd_norm(reg128)
     L.qd_plan_destroy(plan128)
-    L.qd_destroy(reg64)
     L.qd_destroy(reg128)
+    for name in ("exhaustive_analytic", "greedy_analytic", "per_gate"):
+        L.qd_plan_destroy(plans[name])
+
+    # e2e: a user's call sequence with host buffers, every step: the initial
+    # state in from pinned host memory, the planned circuit, all FP64
+    # probabilities out to pinned host memory
+    e2e = None
+    if full or args.c2_ququarts >= 6:
+        host_in = torch.zeros(N, dtype=torch.complex64).pin_memory()
+        host_in[0] = 1.0
+        host_out = torch.empty(N, dtype=torch.float64).pin_memory()
+        hin, hout = host_in.numpy(), host_out.numpy()
+
+        def e2e_step():
+            L.qd_set_amplitudes(reg64, hin)
+            L.qd_plan_run(plans["learned"])
+            L.qd_probabilities(reg64, hout)
+        e2e_step()
+        rep.barrier()
+        e2e_steps = max(2, args.steps // 8)
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            e2e_step()
+        stream.synchronize()
+        e2e_s = rep.max((time.perf_counter() - t0) / e2e_steps)
+        e2e = {"value": world * ngates / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(N * 8),
+               "d2h_bytes_per_step": int(N * 8), "ms_per_step": e2e_s * 1e3,
+               "path": "qd_set_amplitudes(pinned host, complex64) + qd_plan_run + qd_probabilities(pinned host, FP64)",
+               "p_sum_last_step": float(np.sum(hout, dtype=np.float64))}
+        del host_in, host_out
+    L.qd_plan_destroy(plans["learned"])
+    L.qd_destroy(reg64)
     L.qd_model_destroy(model)
-    ms128 = float(np.mean(ts128))
+
+    c1 = c1_summary(L, stream, max(5, args.steps // 2)) if full else None
     kname, kdata = max(kern.items(), key=lambda kv: kv[1][0])
     peak, peak_src = measured_peaks()
     achieved = kdata[1] / (kdata[0] * 1e-3) / 1e9
-    value = aggregate_rate(ngates, world, res["learned"]["ms_per_step"])
+    value = aggregate_rate(ngates, world, ms)
+    tc_files = TC_SOURCES if kname.startswith("tensor_block") else KERNEL_SOURCES
+    traffic = profiled_traffic_scaled(kname, kdata[1] / kdata[2], tc_files)
+    cpu = cpu_baseline_c2(dims, gates) if (rank == 0 and world == 1 and full) else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": res["learned"]["ms_per_step"], "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD_C2 if args.c2_ququarts == 12 else
-                   f"c2 shape with {args.c2_ququarts} ququarts (profiling size)",
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_C2 if full else f"c2 shape with {args.c2_ququarts} ququarts (profiling size)",
+                   "amplitudes": N, "gates": ngates, "precision": "complex64 (FP32 arithmetic)",
                    "plan": "fusion planned with the learned cost model",
-                   "amplitudes": N, "gates": ngates, "precision": "complex64",
-                   "l2": "inputs (34.4 GB) larger than L2", "step": "reset + fused circuit"},
+                   "l2": "inputs (34.4 GB) larger than L2; no flush needed",
+                   "step": "reset to |0...0> + fused circuit (graph replay)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "amp_updates_per_s": value * N,
-        "compare": {"fused_exhaustive": res["exhaustive"], "fused_greedy": res["greedy"],
-                    "fused_learned": res["learned"], "per_gate_complex64": res["per_gate"],
+        "compare": {"fused_learned": res["learned"], "fused_exhaustive_analytic": res["exhaustive_analytic"],
+                    "fused_greedy_analytic": res["greedy_analytic"], "per_gate_complex64": res["per_gate"],
                     "per_gate_complex128": {"ms_per_step": ms128, "gates_per_s": ngates / (ms128 * 1e-3)},
-                    "fused_over_complex128": ms128 / res["learned"]["ms_per_step"],
-                    "fused_over_per_gate_complex64": res["per_gate"]["ms_per_step"] / res["learned"]["ms_per_step"],
-                    "fidelity_fused_c64_vs_c128": abs(ov) ** 2, "norm2_c64": n64, "norm2_c128": n128},
+                    "fused_fp32_over_plain_fp64": ms128 / ms,
+                    "fused_over_per_gate_complex64": res["per_gate"]["ms_per_step"] / ms,
+                    "fidelity_fused_c64_vs_c128": abs(ov) ** 2, "norm2_c64": n64, "norm2_c128": n128,
+                    "c1_per_gate_14_qutrits": c1},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": profiled_traffic_scaled(kname, kdata[1] / kdata[2], TC_SOURCES),
-                     "kernel": kname, "peak_source": peak_src,
-                     "share_of_gate_time": kdata[0] / sum(v[0] for v in kern.values()), "launches": kdata[2]},
+                     "traffic": traffic, "kernel": kname, "peak_source": peak_src,
+                     "share_of_gate_time": kdata[0] / sum(v[0] for v in kern.values()), "launches": kdata[2],
+                     "alg_bytes_per_step": alg_bytes_step,
+                     "step_alg_GB_s": alg_bytes_step / (ms * 1e-3) / 1e9,
+                     "note": "per-launch CUDA events over profiled direct launches; the step's algorithmic "
+                             "bytes over the graph-timed step stay below the copy peak"},
         "kernels": {k: {"ms": v[0], "launches": v[2], "GB_s": v[1] / (v[0] * 1e-3) / 1e9} for k, v in kern.items()},
+        "launch_list": launch_list,
         "clocks": clocks,
+        "e2e": e2e,
+        "gpu_launches": int(args.steps * (res["learned"]["launches"] + 1)),
+        "cpu_baseline": cpu,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -694,6 +827,136 @@ def run_c4(args, rank, world, local):
     rep.close()
     return 0
 
+def run_strides(args, rank, world, local):
+    """Per-gate kernels, one target position at a time, on an HBM-resident
+    register: a Haar single-qudit gate (dense), X_{+1} (permutation), Z
+    (diagonal), a controlled X_{+1} whose control is the next qudit up (or
+    down, for the top qudit), and a Haar two-qudit gate on (q, q+1).  Each
+    launch is timed with CUDA events (median of the repetitions) and reported
+    as algorithmic GB/s and as a fraction of the measured copy peak."""
+    import torch
+
+    from paper_2211_07918_gb300 import qudit as L
+    from paper_2211_07918_gb300 import workloads as wl
+    from paper_2211_07918_gb300.build import build
+
+    build()
+    L.load()
+    torch.cuda.set_device(local)
+    dims = [3] * 18 + [2] * 4 if args.strides_register == "c4" else [2] * 8 + [4] * 12
+    n = len(dims)
+    N = int(np.prod(dims))
+    stream = torch.cuda.Stream(device=torch.device("cuda", local))
+    reg = L.qd_create(dims, None, L.QD_C64, 0, 0, stream.cuda_stream)
+    peak, peak_src = measured_peaks()
+    rng = np.random.default_rng(11)
+    reps = max(3, args.steps)
+    rows = []
+    sampler = ClockSampler(local)
+    sampler.start()
+    for q in range(n):
+        c = q + 1 if q + 1 < n else q - 1
+        cases = [("dense", wl.Gate("U", (q,), matrix=wl.haar_unitary(dims[q], rng))),
+                 ("perm", wl.Gate("X", (q,), param=1)),
+                 ("diag", wl.Gate("Z", (q,), param=1)),
+                 ("ctrl_perm", wl.Gate("X", (q,), (c,), (dims[c] - 1,), 1)),
+                 ("dense2", wl.Gate("U", (q, c), matrix=wl.haar_unitary(dims[q] * dims[c], rng)))]
+        row = {"q": q, "d": dims[q], "stride": int(np.prod(dims[:q])), "control": c}
+        for name, g in cases:
+            plan = L.qd_plan_create(reg, [g], L.QD_PLAN_NONE)
+            L.qd_plan_profile(plan, True)
+            ts, ab, kc = [], 0.0, 0
+            for _ in range(reps + 1):
+                L.qd_plan_run(plan)
+                ms, b_, k_ = L.qd_plan_timings(plan)
+                ts.append(float(ms[0]))
+                ab, kc = float(b_[0]), int(k_[0])
+            L.qd_plan_destroy(plan)
+            t = float(np.median(ts[1:]))
+            gbs = ab / (t * 1e-3) / 1e9
+            row[name] = {"kernel": L.kclass_name(kc), "us": t * 1e3, "GB_s": gbs, "frac": gbs / peak}
+        rows.append(row)
+    clocks = sampler.stop()
+    L.qd_destroy(reg)
+    line = {"metric": "per-gate kernel bandwidth by target stride", "unit": "GB/s", "register": dims,
+            "amplitudes": N, "precision": "complex64", "peak": peak, "peak_source": peak_src,
+            "repetitions": reps, "rows": rows, "clocks": clocks}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+def run_blocks(args, rank, world, local):
+    """Fused dense blocks (two Haar gates whose union spans 2-3 qudits) on the
+    2^32 and 6.2e9-amplitude registers, each timed on the tensor-core kernel
+    (QD_TUNE_TC_MIN_D = 9) and, for D <= 32, on the CUDA-core dense kernel
+    (QD_TUNE_TC_MIN_D = 65): CUDA-event time per launch (median), algorithmic
+    GB/s and fraction of the measured copy peak."""
+    import torch
+
+    from paper_2211_07918_gb300 import qudit as L
+    from paper_2211_07918_gb300 import workloads as wl
+    from paper_2211_07918_gb300.build import build
+
+    build()
+    L.load()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream(device=torch.device("cuda", local))
+    peak, peak_src = measured_peaks()
+    rng = np.random.default_rng(12)
+    reps = max(3, args.steps)
+    cases = {
+        "c2": ([2] * 8 + [4] * 12, [(6, 7, 8), (5, 6, 7), (8, 9), (18, 19), (7, 8, 9), (8, 9, 10), (12, 13, 14),
+                                     (17, 18, 19)]),
+        "c4": ([3] * 18 + [2] * 4, [(0, 1), (8, 9), (17, 18), (19, 20, 21), (16, 17, 18), (17, 18, 19), (0, 1, 2),
+                                     (8, 9, 10), (15, 16, 17)]),
+    }
+    if args.blocks_small:
+        cases = {"c2_small": ([2] * 8 + [4] * 9, [(8, 9, 10), (6, 7, 8)])}
+    out = {}
+    sampler = ClockSampler(local)
+    sampler.start()
+    for name, (dims, sets) in cases.items():
+        reg = L.qd_create(dims, None, L.QD_C64, 0, 0, stream.cuda_stream)
+        rows = []
+        for qs in sets:
+            if len(qs) == 2:
+                gates = [wl.Gate("U", (qs[0],), matrix=wl.haar_unitary(dims[qs[0]], rng)),
+                         wl.Gate("U", (qs[1],), matrix=wl.haar_unitary(dims[qs[1]], rng))]
+            else:
+                a, b, c = qs
+                gates = [wl.Gate("U", (a, b), matrix=wl.haar_unitary(dims[a] * dims[b], rng)),
+                         wl.Gate("U", (b, c), matrix=wl.haar_unitary(dims[b] * dims[c], rng))]
+            D = int(np.prod([dims[q] for q in qs]))
+            row = {"qudits": list(qs), "D": D, "lowest_stride": int(np.prod(dims[:min(qs)]))}
+            for route, tc in (("tensor", 9), ("cuda_core", 65)):
+                if route == "cuda_core" and D > 32:
+                    continue
+                L.qd_set_tuning(reg, L.QD_TUNE_TC_MIN_D, tc)
+                plan = L.qd_plan_create_segmented(reg, gates, [(0, len(gates) - 1)])
+                L.qd_plan_profile(plan, True)
+                ts, ab, kc = [], 0.0, 0
+                for _ in range(reps + 1):
+                    L.qd_plan_run(plan)
+                    ms, b_, k_ = L.qd_plan_timings(plan)
+                    ts.append(float(ms[0]))
+                    ab, kc = float(b_[0]), int(k_[0])
+                err = L.qd_sync(reg)
+                L.qd_plan_destroy(plan)
+                t = float(np.median(ts[1:]))
+                gbs = ab / (t * 1e-3) / 1e9
+                row[route] = {"kernel": L.kclass_name(kc), "ms": t, "GB_s": gbs, "frac": gbs / peak,
+                              "device_error": err}
+            rows.append(row)
+        L.qd_destroy(reg)
+        out[name] = {"register": dims, "amplitudes": int(np.prod(dims)), "rows": rows}
+    clocks = sampler.stop()
+    line = {"metric": "fused block bandwidth, tensor cores vs CUDA cores", "unit": "GB/s", "peak": peak,
+            "peak_source": peak_src, "repetitions": reps, "precision": "complex64", "registers": out,
+            "clocks": clocks}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
 
 def run_ours(args, rank, world, local):
     import torch
@@ -877,13 +1140,17 @@ def main():
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
-    if args.workload == "c2":
-        return run_c2(args, rank, world, local)
+    if args.workload == "c1":
+        return run_ours(args, rank, world, local)
     if args.workload == "c3":
         return run_c3(args, rank, world, local)
     if args.workload == "c4":
         return run_c4(args, rank, world, local)
-    return run_ours(args, rank, world, local)
+    if args.workload == "strides":
+        return run_strides(args, rank, world, local)
+    if args.workload == "blocks":
+        return run_blocks(args, rank, world, local)
+    return run_c2(args, rank, world, local)
 
 
 if __name__ == "__main__":

@@ -68,6 +68,8 @@ extern "C" {
 #define QD_GATE_H 3    /* F_d[j][k] = w^{jk}/sqrt(d) (Sec. 2.1.2) */
 #define QD_GATE_U 4    /* dense user matrix, D x D (Sec. 3.4 User Defined Gate) */
 #define QD_GATE_DIAG 5 /* diagonal user matrix, D entries */
+#define QD_GATE_MEASURE 6 /* measurement flag on all qudits (Sec. 3.4 Measurement Gate, Sec. 3.6 measure_all):
+                             no unitary; every gate after it is ignored.  targets, controls, param ignored */
 
 #define QD_PLAN_NONE 0       /* one kernel per gate, no fusion */
 #define QD_PLAN_GREEDY 1     /* greedy gate fusion into blocks */
@@ -130,10 +132,16 @@ int qd_set_stream(qd_reg *reg, void *stream);
 #define QD_TUNE_TILE_STRIDE 1
 /* QD_TUNE_FUSE_KMAX: most qudits a fused block may span (1..6, default 3).
  * QD_TUNE_FUSE_DMAX: largest dimension of a fused block: complex64 2..64
- * (default 64; blocks with D >= 9 run on the tensor cores as split-BF16
- * products with FP32 accumulation), complex128 2..QD_MAX_D (default 32). */
+ * (default 64), complex128 2..QD_MAX_D (default 32).
+ * QD_TUNE_TC_MIN_D: which kernel runs a complex64 fused dense block of
+ * dimension D <= 32: 0 (default) lets the plan's cost model (analytic, or the
+ * learned model for QD_PLAN_LEARNED) price both and take the cheaper, for D
+ * >= 9; a value in 9..65 sends blocks of D >= value to the tensor cores
+ * (exact BF16 slice products with FP32 accumulation) and smaller ones to the
+ * CUDA-core dense kernels.  Blocks above 32 always run on the tensor cores. */
 #define QD_TUNE_FUSE_KMAX 2
 #define QD_TUNE_FUSE_DMAX 3
+#define QD_TUNE_TC_MIN_D 4
 int qd_set_tuning(qd_reg *reg, int32_t key, int64_t value);
 
 /* ---- gate application, in place (Sec. 2.1.2, Sec. 3.4) ---------------- */
@@ -163,8 +171,53 @@ int qd_apply_cx(qd_reg *reg, int32_t c, int32_t t, int32_t shift, int32_t ctrl_l
  * d_c - 1) (Sec. 2.1.2 multi-controlled Toffoli). */
 int qd_apply_mct(qd_reg *reg, const int32_t *controls, const int32_t *ctrl_levels, int32_t nc,
                  int32_t t, int32_t shift);
-/* Apply one gate record. */
+/* Apply one gate record.  A QD_GATE_MEASURE record sets the register's
+ * measurement flag (qd_measure_all). */
 int qd_apply_gate(qd_reg *reg, const qd_gate *gate);
+
+/* Measurement flag (Sec. 3.4: the Measurement Gate only marks the end of the
+ * circuit; any gate after it is ignored; Sec. 3.6 measure_all).  After
+ * qd_measure_all every later gate call, qd_plan_run, qd_run_circuit and
+ * qd_run_moments on the register returns QD_OK without touching the state,
+ * until qd_reset or qd_set_amplitudes starts a new circuit.  Readouts are
+ * unaffected.  qd_is_measured reports the flag (0 or 1). */
+int qd_measure_all(qd_reg *reg);
+int qd_is_measured(const qd_reg *reg, int32_t *measured);
+
+/* Toffoli through an elevated carrier level (Sec. 3.4: cx((0,1), plus=1),
+ * cx((1,2), plus=1), cx((0,1), plus=2)): X^{d_t}_{+shift} on t when c1 holds
+ * d_c1 - 1 and the carrier holds d_carrier - 2, its top logical level.  The
+ * three generalized CNOTs, each firing on its control's top level d - 1, are
+ * CX_{+1}(c1 -> carrier), CX_{+shift}(carrier -> t), CX_{+(d_carrier-1)}(c1 ->
+ * carrier); the carrier's level d_carrier - 1 is the elevated "|d>" level,
+ * so the carrier needs dimension >= 3 and returns to its input.
+ * qd_toffoli_gates writes the three records (host only, no register needed);
+ * qd_apply_toffoli applies them.  Errors: QD_ERR_ARG (index, shift),
+ * QD_ERR_OVERLAP (repeated qudit), QD_ERR_DIM (carrier dimension < 3). */
+int qd_toffoli_gates(const int32_t *dims, int32_t n, int32_t c1, int32_t carrier, int32_t t, int32_t shift,
+                     qd_gate *out3);
+int qd_apply_toffoli(qd_reg *reg, int32_t c1, int32_t carrier, int32_t t, int32_t shift);
+
+/* Logarithmic-depth multi-controlled Toffoli through |d>-level controls
+ * (Sec. 2.1.2, Fig. 1: controls firing on |d-1> and on |d>): X^{d_t}_{+shift}
+ * on t when every control q holds its active level l_q (ctrl_levels[i], NULL
+ * or -1: d_q - 2).  The controls form a balanced binary tree in heap order
+ * (control i has children 2i+1 and 2i+2); deepest level first, each inner
+ * control is shifted +1 under its children (a leaf child firing on l_u, an
+ * inner child on its elevated level l_u + 1), which raises it to l_v + 1 iff
+ * every control of its subtree is active; then the target fires under the
+ * root; then the raises are undone in reverse order.  Every inner control
+ * needs l_q + 1 < d_q, and the state's values of each control must not exceed
+ * its active level.  Gates: 2 floor(nc / 2) + 1 records with at most two
+ * controls each; depth 2 floor(log2 nc) + 1 (gates of one tree level act on
+ * disjoint qudits).  qd_mct_tree_gates writes *count records to out (NULL
+ * out: count only) and the depth; qd_apply_mct_tree applies them.
+ * Errors: QD_ERR_ARG, QD_ERR_OVERLAP, QD_ERR_DIM (no free level on an inner
+ * control), QD_ERR_OOM (cap < *count). */
+int qd_mct_tree_gates(const int32_t *dims, int32_t n, const int32_t *controls, const int32_t *ctrl_levels, int32_t nc,
+                      int32_t t, int32_t shift, qd_gate *out, int32_t cap, int32_t *count, int32_t *depth);
+int qd_apply_mct_tree(qd_reg *reg, const int32_t *controls, const int32_t *ctrl_levels, int32_t nc, int32_t t,
+                      int32_t shift);
 
 /* ---- circuits ---------------------------------------------------------- */
 
@@ -199,7 +252,8 @@ int qd_plan_destroy(qd_plan *plan);
 #define QD_KCLASS_DENSE_TILE 1
 #define QD_KCLASS_MONO_DIRECT 2
 #define QD_KCLASS_MONO_TILE 3
-#define QD_KCLASS_TENSOR_BLOCK 4 /* fused block on tcgen05 (split-BF16, FP32 accumulate) */
+#define QD_KCLASS_TENSOR_BLOCK 4 /* fused block on tcgen05 (exact BF16 slices, FP32 accumulate) */
+#define QD_KCLASS_DIAG_TABLE 5   /* run of diagonal gates through one table (D = qudits the table covers) */
 int qd_plan_profile(qd_plan *plan, int32_t enable);
 int qd_plan_timings(qd_plan *plan, float *ms, double *alg_bytes, int32_t *kclass);
 /* Plan, run once with direct launches (no graph capture) and release. */
@@ -241,19 +295,38 @@ int qd_sample_u(qd_reg *reg, const double *u, int64_t shots, int64_t *out);
  * device image (512 KiB, held on every GPU that loads the library until the
  * process exits), so n_amplitudes may not exceed 2^28 (QD_ERR_DIM beyond).
  * The first call on each device looks up the array's device address with
- * that device current; make that first call before any stream capture.
+ * that device current; make that first call before any stream capture.  Only
+ * a successful lookup is kept: after a failed one the next call tries again.
  * All calls share the one array: calls whose work overlaps on the GPU (for
  * example on two streams at once) race on it and must be ordered by the
  * caller.  Values an earlier call left in the array are never read.
  * Errors: QD_ERR_ARG (null pointer, bad precision), QD_ERR_DIM, QD_ERR_CUDA. */
 int qd_cdf_noalloc(const void *state, int64_t n_amplitudes, int32_t precision, double *cdf_out, void *stream);
 
+/* Ket readout (Sec. 3.8 OutputType / OutputMethod; Sec. 3.9 prints the
+ * basis states of nonzero probability with their amplitudes): the basis
+ * indices i with |psi_i|^2 > threshold (FP64), in ascending order, found on
+ * the device.  The first min(cap, total) go to indices[] (host) and values[]
+ * (host: method QD_OUT_AMPLITUDE writes re, im per entry, 2 doubles;
+ * QD_OUT_PROBABILITY writes |psi_i|^2, 1 double); *count receives the total
+ * (may exceed cap).  Synchronises.  Errors: QD_ERR_ARG, QD_ERR_OOM. */
+#define QD_OUT_AMPLITUDE 0
+#define QD_OUT_PROBABILITY 1
+int qd_ket_list(qd_reg *reg, int32_t method, double threshold, int64_t cap, int64_t *indices, double *values,
+                int64_t *count);
+/* Ket label of basis index (OutputType.print): "|x_0 x_1 ... x_{n-1}>",
+ * qudit 0 first (the paper prints |120> for x_0 = 1, x_1 = 2, x_2 = 0),
+ * digits in decimal, comma-separated when some dimension exceeds 10.
+ * Host only.  Errors: QD_ERR_ARG, QD_ERR_DIM, QD_ERR_OOM (cap too small). */
+int qd_ket_label(const int32_t *dims, int32_t n, int64_t index, char *buf, int32_t cap);
+
 /* Copy the N amplitudes out of / into the register (register precision). */
 int qd_get_amplitudes(qd_reg *reg, void *out, int32_t where);
 int qd_set_amplitudes(qd_reg *reg, const void *in, int32_t where);
 
 /* Wait for the register's stream; report a device-side error word (0 if
- * none) in *device_error (may be NULL).  Returns QD_ERR_DEVICE if it is set. */
+ * none) in *device_error (may be NULL).  Returns QD_ERR_TIMEOUT when a
+ * bounded wait expired (word 1), QD_ERR_DEVICE for any other nonzero word. */
 int qd_sync(qd_reg *reg, int32_t *device_error);
 
 /* ---- batched persistent execution -------------------------------------- */
@@ -280,6 +353,9 @@ typedef struct qd_batch qd_batch;
                                   level by level within a group, so that a group's states stay in L2
                                   (default 2^25) */
 #define QD_BATCH_TILES_PER_ITEM 5 /* tiles one work item processes (default 1) */
+#define QD_BATCH_POLL_LIMIT 6     /* polls of a work item's wait on its circuit's counter before it gives
+                                     up, skips its tiles and sets the error word to 2 (0..2^30; default
+                                     2^22, over 0.5 s); a small limit makes waits expire on purpose */
 /* ncirc registers; register c has nqudits[c] qudits whose dims follow in
  * dims_concat (concatenated in circuit order).  stream: cudaStream_t as void*. */
 int qd_batch_create(int32_t ncirc, const int32_t *nqudits, const int32_t *dims_concat, void *stream, qd_batch **out);
@@ -300,6 +376,11 @@ int qd_batch_get_amplitudes(qd_batch *b, int32_t c, void *out);
 /* Total amplitudes, work items of a run, launches per run, and the device
  * error word (synchronises; nonzero: a bounded wait expired). */
 int qd_batch_info(qd_batch *b, int64_t *total_amplitudes, int32_t *items, int32_t *launches, int32_t *device_error);
+/* Wait for the batch's stream and report the last run's device error word:
+ * QD_ERR_TIMEOUT when a work item's bounded wait expired (word 2; the run's
+ * results are not valid), QD_ERR_DEVICE for any other nonzero word (3: a
+ * gate descriptor failed its bounds check).  Each run clears the word. */
+int qd_batch_sync(qd_batch *b, int32_t *device_error);
 /* Profiling mode: runs launch directly (no graph) with CUDA events around the
  * persistent kernel.  qd_batch_timings (synchronises) returns that kernel's
  * time in the last run and its algorithmic bytes (every segment reads and
@@ -361,6 +442,37 @@ int qd_segment_features(qd_reg *reg, const qd_gate *gates, int32_t ngates, int32
  * QD_TUNE_FUSE_*, up to 6 qudits and D <= 64 (complex64) or 32 (complex128). */
 int qd_plan_create_segmented(qd_reg *reg, const qd_gate *gates, int32_t ngates, const int32_t *seg_first,
                              const int32_t *seg_last, int32_t nseg, qd_plan **out);
+
+/* ---- QuDiet QASM front end (Sec. 4) ----------------------------------- */
+/* Parse a QuDiet QASM program: ".qudit n"; n declarations "qudit NAME (d)" in
+ * qudit order (the first declared is qudit 0); ".begin"; gate lines "X q [a]"
+ * (X^d_{+a}, a = 1 if absent), "Z q [p]" (Z_d^p, p = 1 if absent), "H q"
+ * (F_d), "CX c t [a]" (X^{d_t}_{+a} on t when c holds d_c - 1); ".end".
+ * Names are case-insensitive; '#' or "//" starts a comment.  Writes the dims
+ * (dims_cap entries) and gate records (gates_cap entries; named gates carry
+ * no matrix), *n and *ngates the counts (written also when an array is too
+ * small, which returns QD_ERR_OOM; NULL arrays query the counts).  On a
+ * syntax error *error_line is the 1-based line.  Errors: QD_ERR_ARG
+ * (syntax, unknown name or gate, shift out of [1, d-1]), QD_ERR_DIM
+ * (dimension outside [2, 64]), QD_ERR_OVERLAP (CX on one qudit). */
+int qd_qasm_parse(const char *text, int32_t *dims, int32_t dims_cap, int32_t *n, qd_gate *gates, int32_t gates_cap,
+                  int32_t *ngates, int32_t *error_line);
+
+/* ---- the paper's execution model, for comparison (Sec. 3.5-3.6) -------- */
+/* Apply the gate list to the register's current state the way the paper's
+ * backends do: gates are packed into moments (each gate in the first moment
+ * after the last one holding a gate on any of its qudits), every moment
+ * becomes its full N x N Kronecker-product operator with identities on the
+ * untouched qudits, the operators are multiplied from the last moment down
+ * to the first (GEMM chain) and the product is applied to the state (GEMV),
+ * all in complex128 on the device.  Registers of at most 4096 amplitudes
+ * (QD_ERR_DIM beyond); allocates three N x N operators per call;
+ * synchronises.  *n_moments (may be NULL) receives the moment count. */
+int qd_run_moments(qd_reg *reg, const qd_gate *gates, int32_t ngates, int32_t *n_moments);
+/* Host only: the moment of every gate (-1 for gates dropped as identities or
+ * after a measurement flag) and the moment count. */
+int qd_moment_packing(const int32_t *dims, int32_t n, const qd_gate *gates, int32_t ngates, int32_t *moment_of_gate,
+                      int32_t *n_moments);
 
 /* Static message for an error code; thread-local message of the last failure. */
 const char *qd_strerror(int code);

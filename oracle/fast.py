@@ -69,8 +69,12 @@ def apply(psi: np.ndarray, dims, gate, nthreads: int = 0) -> None:
 
 
 def run_circuit(dims, gates, init_levels=None, nthreads: int = 0, psi0=None) -> np.ndarray:
+    """Gates in order; a "MEASURE" record ends the circuit (Sec. 3.4: gates
+    after the Measurement Gate are ignored)."""
     psi = qo.basis_state(dims, init_levels) if psi0 is None else np.array(psi0, dtype=np.complex128)
     for g in gates:
+        if getattr(g, "kind", None) == "MEASURE":
+            break
         apply(psi, dims, g, nthreads)
     return psi
 

@@ -382,10 +382,16 @@ def _check_acting(dims, targets, controls, levels):
 
 def run_circuit(dims: Sequence[int], gates: Iterable, init_levels=None, mode: str = "loop",
                 psi0: np.ndarray | None = None) -> np.ndarray:
-    """Evolve the initial product state through a gate list in the given mode."""
+    """Evolve the initial product state through a gate list in the given mode.
+
+    A record of kind "MEASURE" is the paper's Measurement Gate: it has no
+    unitary, marks the end of the circuit, and every gate after it is ignored
+    (Sec. 3.4, "Measurement Gate"; Sec. 3.6, measure_all)."""
     psi = basis_state(dims, init_levels) if psi0 is None else np.array(psi0, dtype=np.complex128)
     step = {"loop": loop_apply, "dense": dense_apply, "python": loop_apply_python}[mode]
     for g in gates:
+        if getattr(g, "kind", None) == "MEASURE":
+            break
         psi = step(psi, dims, g)
     return psi
 

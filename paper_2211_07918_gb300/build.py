@@ -30,6 +30,10 @@ SOURCES = [
     "qd_tc.cu",
     "qd_mlp.cu",
     "qd_batch.cu",
+    "qd_ket.cu",
+    "qd_circuit.cu",
+    "qd_kron.cu",
+    "qd_diag.cu",
 ]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -45,12 +45,52 @@ def register_size(dims: Sequence[int]) -> int:
     return int(np.prod([int(d) for d in dims]))
 
 
+def random_diag_run(rng: np.random.Generator, dims: Sequence[int]):
+    """2-10 diagonal gates (phases on one qudit, controlled phases, two-qudit
+    phase tables) spread over a contiguous range of 4-12 qudits whose table
+    has at most 2^22 entries: one diagonal-run launch."""
+    n = len(dims)
+    for _ in range(50):
+        width = int(rng.integers(4, min(12, n) + 1))
+        lo = int(rng.integers(0, n - width + 1))
+        if int(np.prod(dims[lo:lo + width])) <= (1 << 22):
+            break
+    else:
+        lo, width = 0, 4
+    qs = list(range(lo, lo + width))
+    out = []
+    for _ in range(int(rng.integers(2, 11))):
+        r = rng.random()
+        if r < 0.3:
+            q = int(rng.choice(qs))
+            out.append(Gate("Z", (q,), param=int(rng.integers(1, dims[q]))))
+        elif r < 0.7:
+            c, t = (int(x) for x in rng.choice(qs, size=2, replace=False))
+            out.append(Gate("DIAG", (t,), (c,), (int(rng.integers(0, dims[c])),),
+                            matrix=np.exp(2j * np.pi * rng.random(dims[t]))))
+        else:
+            a, b = (int(x) for x in rng.choice(qs, size=2, replace=False))
+            out.append(Gate("DIAG", (a, b), matrix=np.exp(2j * np.pi * rng.random(dims[a] * dims[b]))))
+    # make the run span more than three qudits (beyond the block limit)
+    used = {q for g in out for q in tuple(g.targets) + tuple(g.controls or ())}
+    for q in qs:
+        if len(used) > 3:
+            break
+        if q not in used:
+            out.append(Gate("Z", (q,), param=1))
+            used.add(q)
+    return out
+
+
 def random_launch(rng: np.random.Generator, dims: Sequence[int], dmax: int = 64):
     """Gates that form one launch: a single permutation/diagonal gate, a
-    single dense gate, a fused block of two dense gates over 2-3 qudits, or
-    a fused block of 2-4 permutations with phases over 2-3 qudits."""
+    single dense gate, a fused block of two dense gates over 2-3 qudits, a
+    fused block of 2-4 permutations with phases over 2-3 qudits, or a run of
+    diagonal gates over 4-12 qudits."""
     n = len(dims)
-    kind = rng.choice(["mono", "dense", "block", "block", "monoblock"])
+    kind = rng.choice(["mono", "dense", "block", "block", "block", "monoblock", "diagrun"])
+    if kind == "diagrun":
+        return random_diag_run(rng, dims)
     if kind == "monoblock":
         # fused permutations with phases (shifts, clocks, controlled shifts)
         # on 2-3 qudits: the product runs on the mono kernel
@@ -146,6 +186,9 @@ def generate(n_samples: int, seed: int = 0, registers: Iterable[Sequence[int]] =
                 if len(y) >= n_samples:
                     break
                 gates = random_launch(rng, dims, 64 if precision == L.QD_C64 else 32)
+                # dense blocks of D <= 32 are timed on either kernel (the
+                # features record which), so that the model can price both
+                L.qd_set_tuning(h, L.QD_TUNE_TC_MIN_D, 9 if rng.random() < 0.5 else 65)
                 ga = L.GateArray(gates)
                 f = L.qd_segment_features(h, ga, 0, len(gates) - 1)
                 ms = time_launch(h, gates, reps)
@@ -163,6 +206,20 @@ def train(X, y, epochs: int = 80, batch: int = 256, lr: float = 2e-3, seed: int 
     m = L.qd_model_create()
     loss = L.qd_model_train(m, X, y, epochs, batch, lr, seed)
     return m, loss
+
+
+def kernel_source_sha() -> str:
+    """Hash of the library's CUDA and host sources: the kernels a set of
+    training timings was taken on."""
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(HERE, "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(f.encode())
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def save(model: int, path: str = DEFAULT_WEIGHTS, **meta) -> None:
@@ -215,24 +272,40 @@ def plan_time(reg: int, gates, plan_kind=None, segments=None, reps: int = 3) -> 
         L.qd_plan_destroy(plan)
 
 
+def _is_diag(g) -> bool:
+    return g.kind in ("Z", "DIAG")
+
+
 def exhaustive_measured(reg: int, dims: Sequence[int], gates, kmax: int = 3, dmax: int = 64, reps: int = 3):
     """The measured optimum: the minimum-time contiguous segmentation, where every
     candidate segment's cost is its measured launch time (dynamic program
     over prefixes; a segment of several gates must span <= kmax qudits of
-    total dimension <= dmax).  Returns (segments, summed measured ms)."""
+    total dimension <= dmax, or be a run of diagonal gates whose covering
+    qudit range gives a table of <= 2^24 entries; a dense block of D <= 32 is
+    timed on the CUDA cores and on the tensor cores and the faster counts).
+    Returns (segments, summed measured ms)."""
     n = len(gates)
     cost = {}
     best = [0.0] + [math.inf] * n
     back = [-1] * (n + 1)
     for i in range(1, n + 1):
         qs = set()
+        all_diag = True
         for j in range(i - 1, -1, -1):
             qs |= set(gates[j].controls or ()) | set(gates[j].targets)
-            if j < i - 1 and (len(qs) > kmax or int(np.prod([dims[q] for q in qs])) > dmax):
+            all_diag = all_diag and _is_diag(gates[j])
+            in_block = len(qs) <= kmax and int(np.prod([dims[q] for q in qs])) <= dmax
+            in_run = all_diag and int(np.prod(dims[min(qs):max(qs) + 1])) <= (1 << 24)
+            if j < i - 1 and not (in_block or in_run):
                 break  # unions only grow as j decreases
             seg = (j, i - 1)
             if seg not in cost:
-                cost[seg] = time_launch(reg, gates[j:i], reps)
+                ts = []
+                for tc in (9, 65):
+                    L.qd_set_tuning(reg, L.QD_TUNE_TC_MIN_D, tc)
+                    ts.append(time_launch(reg, gates[j:i], reps))
+                L.qd_set_tuning(reg, L.QD_TUNE_TC_MIN_D, 0)
+                cost[seg] = min(ts)
             c = best[j] + cost[seg]
             if c < best[i]:
                 best[i], back[i] = c, j
@@ -260,8 +333,8 @@ def evaluate(model: int, n_circuits: int = 4, seed: int = 7000, spectators=(3, 3
                    "exhaustive_analytic": plan_time(h, gates, L.QD_PLAN_EXHAUSTIVE, reps=reps),
                    "learned": plan_time(h, gates, L.QD_PLAN_LEARNED, reps=reps)}
             if measured:
-                segs, _ = exhaustive_measured(h, dims, gates, reps=reps)
-                row["measured_optimum"] = plan_time(h, gates, segments=segs, reps=reps)
+                segs, opt = exhaustive_measured(h, dims, gates, reps=reps)
+                row["measured_optimum"] = opt
             rows.append(row)
             if log:
                 log(str(row))
@@ -315,11 +388,13 @@ def main(argv=None):
     pred = L.qd_model_predict(m, X[te])
     resid = pred - y[te]
     r2 = 1.0 - float(np.sum(resid ** 2) / np.sum((y[te] - y[te].mean()) ** 2))
-    save(m, args.out, samples=n, train_loss=loss, test_r2=r2, test_rmse_log=float(np.sqrt(np.mean(resid ** 2))))
+    save(m, args.out, samples=n, train_loss=loss, test_r2=r2, test_rmse_log=float(np.sqrt(np.mean(resid ** 2))),
+         source_sha=kernel_source_sha(), seed=args.seed)
     np.savez(os.path.splitext(args.out)[0] + "_data.npz", X=X, y=y)
     rows = evaluate(m, args.circuits, measured=not args.no_measured_optimum, log=log)
     tot = {k: float(sum(r[k] for r in rows)) for k in rows[0] if k not in ("N", "gates")}
     print(json.dumps({"samples": n, "gen_s": gen_s, "train_loss": loss, "test_r2": r2,
+                      "source_sha": kernel_source_sha(),
                       "test_rmse_log": float(np.sqrt(np.mean(resid ** 2))), "plan_ms_totals": tot,
                       "circuits": rows}), flush=True)
     L.qd_model_destroy(m)

@@ -29,6 +29,9 @@
 #include "qd_mlp.h"
 #include "qd_plan.h"
 #include "qd_reduce.h"
+#include "qd_ket.h"
+#include "qd_kron.h"
+#include "qd_diag.h"
 #include "qd_tc.h"
 
 using namespace qd;
@@ -76,7 +79,9 @@ struct qd_reg {
     int64_t tile_stride = -1;  // -1: process default
     int32_t fuse_kmax = 3;     // largest number of qudits of a fused block
     int32_t fuse_dmax = -1;    // largest dimension of a fused block (-1: 64 for c64, 32 for c128)
+    int32_t tc_min_d = 0;      // complex64 fused blocks of D >= this on the tensor cores (0: the cost model decides)
     qd_model *model = nullptr; // learned cost model for QD_PLAN_LEARNED
+    bool measured = false;     // measurement flag set: later gates are ignored (Sec. 3.4)
 };
 
 struct qd_plan {
@@ -84,10 +89,12 @@ struct qd_plan {
     std::vector<GatePlan> gates;
     int32_t blocks = 0;
     void *tc_buf = nullptr;  // device: BF16 terms of every tensor-core block
+    void *tab_buf = nullptr; // device: tables of every diagonal run
     bool profile = false;
     std::vector<cudaEvent_t> events;  // launches + 1 when profiling
     bool use_graph = true;            // capture on first run, replay afterwards
     std::atomic<int> gate_open{1};    // profiling: holds the stream until every launch is enqueued
+    bool measure_after = false;       // the gate list ended with the measurement flag
     cudaGraphExec_t exec = nullptr;   // captured launches (non-default streams)
     void drop_graph() {
         if (exec) cudaGraphExecDestroy(exec);
@@ -97,6 +104,7 @@ struct qd_plan {
         drop_graph();
         for (cudaEvent_t e : events) cudaEventDestroy(e);
         if (tc_buf) cudaFree(tc_buf);
+        if (tab_buf) cudaFree(tab_buf);
     }
 };
 
@@ -126,6 +134,8 @@ int reg_ok(const qd_reg *r) {
 
 cudaError_t launch_plan(const qd_reg *r, const GatePlan &g) {
     if (g.mode == Mode::Tensor) return launch_block_tc(g, r->psi, r->sm_count, r->dev_err, r->stream);
+    if (g.mode == Mode::Table)
+        return diag_table_apply(r->psi, r->prec, (uint64_t)r->N, g.tab_div, g.tab_size, g.tab, r->sm_count, r->stream);
     if (r->prec == QD_C64) return launch_gate_f32(g, r->psi, r->sm_count, r->stream);
     return launch_gate_f64(g, r->psi, r->sm_count, r->stream);
 }
@@ -493,6 +503,11 @@ int prepare_gate(const qd_reg *r, const qd_gate *gt, GatePlan &g, bool *noop) {
 }
 
 int apply_record(qd_reg *r, const qd_gate *gt) {
+    if (gt->kind == QD_GATE_MEASURE) {  // the flag that ends the circuit (Sec. 3.4)
+        r->measured = true;
+        return QD_OK;
+    }
+    if (r->measured) return QD_OK;  // a gate after the measurement flag is ignored
     GatePlan g;
     bool noop = false;
     int rc = prepare_gate(r, gt, g, &noop);
@@ -680,6 +695,20 @@ int qd_reset(qd_reg *r, const int32_t *init_levels) {
         idx += (int64_t)l * r->s[q];
     }
     QD_CUDA(init_basis(r->psi, r->prec, (uint64_t)r->N, (uint64_t)idx, r->sm_count, r->stream));
+    r->measured = false;
+    return QD_OK;
+}
+
+int qd_measure_all(qd_reg *r) {
+    if (int rc = reg_ok(r)) return rc;
+    r->measured = true;
+    return QD_OK;
+}
+
+int qd_is_measured(const qd_reg *r, int32_t *measured) {
+    if (int rc = reg_ok(r)) return rc;
+    if (!measured) return fail(QD_ERR_ARG, "null output");
+    *measured = r->measured ? 1 : 0;
     return QD_OK;
 }
 
@@ -715,6 +744,11 @@ int qd_set_tuning(qd_reg *r, int32_t key, int64_t value) {
             r->fuse_dmax = (int32_t)value;
             return QD_OK;
         }
+        case QD_TUNE_TC_MIN_D:
+            if (value != 0 && (value < kTcMinD || value > kTcMaxD + 1))
+                return fail(QD_ERR_ARG, "tensor-core block threshold must be 0 (cost model) or in [9, 65]");
+            r->tc_min_d = (int32_t)value;
+            return QD_OK;
         default:
             return fail(QD_ERR_ARG, "unknown tuning key");
     }
@@ -777,7 +811,13 @@ int qd_apply_gate(qd_reg *r, const qd_gate *gate) {
 
 namespace {
 
-RegisterShape shape_of(const qd_reg *r) { return RegisterShape{r->n, r->dims, r->s, r->N, r->prec}; }
+RegisterShape shape_of(const qd_reg *r) { return RegisterShape{r->n, r->dims, r->s, r->N, r->prec, r->tc_min_d}; }
+
+bool has_measure(const qd_gate *gates, int32_t ngates) {
+    for (int i = 0; i < ngates; ++i)
+        if (gates[i].kind == QD_GATE_MEASURE) return true;
+    return false;
+}
 
 // Validate every gate, drop identities, and collect both the fusion view
 // (matrix over controls + targets) and the original records.
@@ -785,6 +825,7 @@ int collect_gates(const qd_reg *r, const qd_gate *gates, int32_t ngates, std::ve
                   std::vector<const qd_gate *> &orig) {
     for (int i = 0; i < ngates; ++i) {
         const qd_gate *gt = &gates[i];
+        if (gt->kind == QD_GATE_MEASURE) break;  // gates after the measurement flag are ignored (Sec. 3.4)
         Acting a;
         int rc = validate(r, gt->targets, gt->k, gt->controls, gt->ctrl_levels, gt->nc, a);
         if (rc == QD_OK) {
@@ -805,6 +846,9 @@ int collect_gates(const qd_reg *r, const qd_gate *gates, int32_t ngates, std::ve
                 }
                 std::vector<int> c(a.c, a.c + a.nc), lv(a.lv, a.lv + a.nc), t(a.t, a.t + a.k);
                 fg.push_back(make_fuse_gate(c, lv, t, M, r->dims, g.kind == Kind::Mono));
+                bool ident = g.kind == Kind::Mono;  // a permutation with phases whose permutation is the identity
+                for (int j = 0; ident && j < a.D; ++j) ident = g.src[j] == j;
+                fg.back().diag = ident;
                 orig.push_back(gt);
             }
         }
@@ -823,11 +867,14 @@ CostFn cost_for(const qd_reg *r, int plan_kind) {
 }
 
 int segments_for(const qd_reg *r, const std::vector<FuseGate> &fg, int plan_kind,
-                 std::vector<std::pair<int, int>> &segs, double *model_cost) {
+                 std::vector<std::pair<int, int>> &segs, std::vector<int> &kinds, double *model_cost) {
     const RegisterShape sh = shape_of(r);
     const int kmax = r->fuse_kmax;
     const int dmax = r->fuse_dmax > 0 ? r->fuse_dmax : (r->prec == QD_C64 ? kTcMaxD : QD_MAX_D);
     CostFn cost = cost_for(r, plan_kind);
+    // learned costs of every candidate segment; declared here because the
+    // final cost function, used after the switch, refers to it
+    std::map<std::array<float, kFeatures>, double> table;
     switch (plan_kind) {
         case QD_PLAN_NONE:
             segs.clear();
@@ -843,7 +890,6 @@ int segments_for(const qd_reg *r, const std::vector<FuseGate> &fg, int plan_kind
             if (!r->model) return fail(QD_ERR_UNSUPPORTED, "QD_PLAN_LEARNED needs a cost model (qd_set_cost_model)");
             // every feasible candidate segment, predicted in one batched inference
             std::vector<std::array<float, kFeatures>> feats;
-            std::map<std::array<float, kFeatures>, double> table;
             CostFn collect = [&](const LaunchFeatures &f) {
                 std::array<float, kFeatures> k;
                 std::copy(f.f, f.f + kFeatures, k.begin());
@@ -855,7 +901,7 @@ int segments_for(const qd_reg *r, const std::vector<FuseGate> &fg, int plan_kind
             for (auto &k : feats) X.insert(X.end(), k.begin(), k.end());
             if (int rc = qd_model_predict(r->model, X.data(), (int32_t)feats.size(), y.data())) return rc;
             for (size_t i = 0; i < feats.size(); ++i) table[feats[i]] = std::exp((double)y[i]) * 1e-6;
-            CostFn learned = [&](const LaunchFeatures &f) {
+            CostFn learned = [&table, sh](const LaunchFeatures &f) {
                 std::array<float, kFeatures> k;
                 std::copy(f.f, f.f + kFeatures, k.begin());
                 auto it = table.find(k);
@@ -868,11 +914,12 @@ int segments_for(const qd_reg *r, const std::vector<FuseGate> &fg, int plan_kind
         default:
             return fail(QD_ERR_ARG, "unknown plan kind");
     }
-    if (model_cost) {
-        double c = 0.0;
-        for (auto &sg : segs) c += segment_cost(fg, sg.first, sg.second, sh, cost);
-        *model_cost = c;
-    }
+    // the kernel of every segment, as the final cost function priced it
+    double c = 0.0;
+    kinds.assign(segs.size(), 0);
+    for (size_t i = 0; i < segs.size(); ++i)
+        c += segment_cost(fg, segs[i].first, segs[i].second, sh, cost, kmax, &kinds[i]);
+    if (model_cost) *model_cost = c;
     return QD_OK;
 }
 
@@ -906,6 +953,58 @@ int plan_block_tc(const qd_reg *r, const FuseBlock &b, GatePlan &g, std::vector<
     return QD_OK;
 }
 
+// A diagonal run awaiting its table: covered range, gates and their diagonals.
+struct DiagRunSpec {
+    int plan_index = 0;  // position of its GatePlan in the plan
+    DiagRange range{};
+    std::vector<DiagGateDesc> gates;
+    std::vector<double> pool;  // interleaved complex diagonal entries of every gate
+};
+
+// Plan of a diagonal run gates[first..last] (every gate diagonal): the
+// covered qudit range [qa, qb], each gate's acting qudits as range positions
+// and its full diagonal (controls included) from its matrix over them.
+int plan_diag_run(const qd_reg *r, const std::vector<FuseGate> &fg, int first, int last, GatePlan &g,
+                  DiagRunSpec &spec) {
+    static_assert(kDiagRunMaxTable == kDiagTableMax, "diagonal table limits of the planner and kernel differ");
+    int qa = r->n, qb = -1;
+    for (int i = first; i <= last; ++i)
+        for (int q : fg[i].acting) {
+            qa = std::min(qa, q);
+            qb = std::max(qb, q);
+        }
+    if (qb - qa + 1 > kDiagMaxRange) return fail(QD_ERR_DIM, "diagonal run spans too many qudits");
+    g = GatePlan{};
+    g.mode = Mode::Table;
+    g.kind = Kind::Mono;
+    g.N = (uint64_t)r->N;
+    g.tab_div = (uint64_t)r->s[qa];
+    uint64_t TS = 1;
+    spec.range.nr = qb - qa + 1;
+    for (int q = qa; q <= qb; ++q) {
+        spec.range.d[q - qa] = r->dims[q];
+        TS *= (uint64_t)r->dims[q];
+    }
+    if (TS > kDiagTableMax) return fail(QD_ERR_DIM, "diagonal run table too large");
+    g.tab_size = TS;
+    g.D = spec.range.nr;  // reported as the kernel class's D: qudits of the covered range
+    g.alg_bytes = 2.0 * (double)r->N * (double)r->esize;
+    for (int i = first; i <= last; ++i) {
+        const FuseGate &x = fg[i];
+        if ((int)x.acting.size() > kDiagMaxActing) return fail(QD_ERR_DIM, "diagonal gate acts on too many qudits");
+        DiagGateDesc d{};
+        d.nq = (int32_t)x.acting.size();
+        for (int m = 0; m < d.nq; ++m) d.q[m] = x.acting[m] - qa;
+        d.off = (int64_t)(spec.pool.size() / 2);
+        for (int j = 0; j < x.Dact; ++j) {
+            spec.pool.push_back(x.M[2 * ((size_t)j * x.Dact + j)]);
+            spec.pool.push_back(x.M[2 * ((size_t)j * x.Dact + j) + 1]);
+        }
+        spec.gates.push_back(d);
+    }
+    return QD_OK;
+}
+
 // Launch plan of one fused block: a dense gate on the block's qudits.
 int plan_block(const qd_reg *r, const FuseBlock &b, GatePlan &g) {
     Acting a;
@@ -931,26 +1030,48 @@ namespace {
 // blocks must respect the register's QD_TUNE_FUSE_* limits (planner output
 // does by construction; explicit segmentations only need the hard limits).
 int build_plan(qd_reg *r, const std::vector<FuseGate> &fg, const std::vector<const qd_gate *> &orig,
-               const std::vector<std::pair<int, int>> &segs, qd_plan **out) {
+               const std::vector<std::pair<int, int>> &segs, const std::vector<int> &kinds, qd_plan **out) {
     qd_plan *p = new qd_plan();
     p->reg = r;
     p->gates.reserve(segs.size());
     std::vector<std::vector<uint16_t>> tc_terms;
     std::vector<int> tc_index;
+    std::vector<DiagRunSpec> runs;
+    const RegisterShape sh = shape_of(r);
     int rc = QD_OK;
-    for (auto &sg : segs) {
+    for (size_t si = 0; si < segs.size(); ++si) {
+        const auto &sg = segs[si];
         GatePlan g;
         if (sg.first == sg.second) {
             bool noop = false;
             rc = prepare_gate(r, orig[sg.first], g, &noop);
             if (rc == QD_OK && noop) continue;
         } else {
+            bool all_mono = true, all_diag = true;  // the product is then a permutation with phases / a diagonal
+            std::vector<int> uq;
+            for (int i = sg.first; i <= sg.second; ++i) {
+                all_mono = all_mono && fg[i].mono;
+                all_diag = all_diag && fg[i].diag;
+                for (int q : fg[i].acting)
+                    if (std::find(uq.begin(), uq.end(), q) == uq.end()) uq.push_back(q);
+            }
+            (void)sh;
+            if (kinds[si] == kKernelDiagTable) {
+                runs.emplace_back();
+                runs.back().plan_index = (int)p->gates.size();
+                rc = plan_diag_run(r, fg, sg.first, sg.second, g, runs.back());
+                if (rc == QD_OK) {
+                    ++p->blocks;
+                    p->gates.push_back(g);
+                    continue;
+                }
+                delete p;
+                return rc;
+            }
             FuseBlock b = build_block(fg, sg.first, sg.second, r->dims);
-            bool all_mono = true;  // the product is then a permutation with phases (mono kernel)
-            for (int i = sg.first; i <= sg.second; ++i) all_mono = all_mono && fg[i].mono;
             if ((int)b.qudits.size() > QD_MAX_TARGETS) {
                 rc = fail(QD_ERR_DIM, "fused block spans more than 6 qudits");
-            } else if (r->prec == QD_C64 && b.D >= kTcMinD && b.D <= kTcMaxD && !(all_mono && b.D <= kMonoBlockMaxD)) {
+            } else if (b.D <= kTcMaxD && kinds[si] == kKernelBlockTc) {
                 tc_terms.emplace_back();
                 rc = plan_block_tc(r, b, g, tc_terms.back());
                 tc_index.push_back((int)p->gates.size());
@@ -987,6 +1108,41 @@ int build_plan(qd_reg *r, const std::vector<FuseGate> &fg, const std::vector<con
             off += (tc_terms[i].size() * 2 + 255) / 256 * 256;
         }
     }
+    if (!runs.empty()) {  // one device buffer for every diagonal run's table, built on the device
+        const size_t esz = 16;  // float4 (hi, lo) or double2
+        size_t total = 0;
+        for (auto &ru : runs) total += (p->gates[ru.plan_index].tab_size * esz + 255) / 256 * 256;
+        if (cudaMalloc(&p->tab_buf, total) != cudaSuccess) {
+            cudaGetLastError();
+            p->tab_buf = nullptr;
+            delete p;
+            return fail(QD_ERR_OOM, "diagonal run table allocation failed");
+        }
+        size_t off = 0;
+        for (auto &ru : runs) {
+            GatePlan &gp = p->gates[ru.plan_index];
+            char *dst = static_cast<char *>(p->tab_buf) + off;
+            DiagGateDesc *dg = nullptr;
+            double2 *pool = nullptr;
+            cudaError_t e = cudaMalloc(&dg, sizeof(DiagGateDesc) * ru.gates.size());
+            if (e == cudaSuccess) e = cudaMalloc(&pool, sizeof(double) * ru.pool.size());
+            if (e == cudaSuccess)
+                e = cudaMemcpy(dg, ru.gates.data(), sizeof(DiagGateDesc) * ru.gates.size(), cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = cudaMemcpy(pool, ru.pool.data(), sizeof(double) * ru.pool.size(), cudaMemcpyHostToDevice);
+            if (e == cudaSuccess)
+                e = diag_table_build(dst, r->prec, gp.tab_size, ru.range, dg, (int32_t)ru.gates.size(), pool,
+                                     r->sm_count, r->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
+            if (dg) cudaFree(dg);
+            if (pool) cudaFree(pool);
+            if (e != cudaSuccess) {
+                delete p;
+                return cuda_fail(e, "diagonal run table");
+            }
+            gp.tab = dst;
+            off += (gp.tab_size * esz + 255) / 256 * 256;
+        }
+    }
     *out = p;
     return QD_OK;
 }
@@ -1005,8 +1161,11 @@ int qd_plan_create(qd_reg *r, const qd_gate *gates, int32_t ngates, int32_t plan
     int rc = collect_gates(r, gates, ngates, fg, orig);
     if (rc) return rc;
     std::vector<std::pair<int, int>> segs;
-    if ((rc = segments_for(r, fg, plan_kind, segs, nullptr))) return rc;
-    return build_plan(r, fg, orig, segs, out);
+    std::vector<int> kinds;
+    if ((rc = segments_for(r, fg, plan_kind, segs, kinds, nullptr))) return rc;
+    rc = build_plan(r, fg, orig, segs, kinds, out);
+    if (rc == QD_OK) (*out)->measure_after = has_measure(gates, ngates);
+    return rc;
 }
 
 int qd_plan_create_segmented(qd_reg *r, const qd_gate *gates, int32_t ngates, const int32_t *seg_first,
@@ -1042,7 +1201,17 @@ int qd_plan_create_segmented(qd_reg *r, const qd_gate *gates, int32_t ngates, co
         const int64_t cap = r->prec == QD_C64 ? kTcMaxD : QD_MAX_D;
         if ((int)qs.size() > QD_MAX_TARGETS || D > cap) return fail(QD_ERR_DIM, "segment block too large");
     }
-    return build_plan(r, fg, orig, segs, out);
+    // kernels of the given segments as the register's cost model prices them
+    std::vector<int> kinds(segs.size(), 0);
+    {
+        const RegisterShape sh = shape_of(r);
+        const CostFn cost = cost_for(r, QD_PLAN_GREEDY);
+        for (size_t i = 0; i < segs.size(); ++i)
+            segment_cost(fg, segs[i].first, segs[i].second, sh, cost, r->fuse_kmax, &kinds[i]);
+    }
+    rc = build_plan(r, fg, orig, segs, kinds, out);
+    if (rc == QD_OK) (*out)->measure_after = has_measure(gates, ngates);
+    return rc;
 }
 
 int qd_set_cost_model(qd_reg *r, qd_model *model) {
@@ -1063,7 +1232,7 @@ int qd_segment_features(qd_reg *r, const qd_gate *gates, int32_t ngates, int32_t
         std::copy(f.f, f.f + kFeatures, out);
         return 0.0;
     };
-    segment_cost(fg, first, last, sh, grab);
+    segment_cost(fg, first, last, sh, grab, r->fuse_kmax);
     return QD_OK;
 }
 
@@ -1100,6 +1269,8 @@ void CUDART_CB hold_until_open(void *arg) {
 
 int qd_plan_run(qd_plan *p) {
     if (!p) return fail(QD_ERR_ARG, "null plan");
+    if (p->reg->measured) return QD_OK;  // gates after the measurement flag are ignored (Sec. 3.4)
+    if (p->measure_after) p->reg->measured = true;  // set now: the launches below are still ordered before any later call
     cudaStream_t s = p->reg->stream;
     if (p->profile) {  // events cannot be timed inside a graph: direct launches behind a hold
         QD_CUDA(cudaStreamSynchronize(s));
@@ -1167,6 +1338,7 @@ int qd_plan_timings(qd_plan *p, float *ms, double *alg_bytes, int32_t *kclass) {
             int c = g.kind == Kind::Dense ? (g.mode == Mode::Direct ? QD_KCLASS_DENSE_DIRECT : QD_KCLASS_DENSE_TILE)
                                           : (g.mode == Mode::Direct ? QD_KCLASS_MONO_DIRECT : QD_KCLASS_MONO_TILE);
             if (g.mode == Mode::Tensor) c = QD_KCLASS_TENSOR_BLOCK;
+            if (g.mode == Mode::Table) c = QD_KCLASS_DIAG_TABLE;
             kclass[i] = c | (g.D << 8);
         }
     }
@@ -1316,6 +1488,87 @@ int qd_set_amplitudes(qd_reg *r, const void *in, int32_t where) {
     if (where != QD_HOST && where != QD_DEVICE) return fail(QD_ERR_ARG, "where must be QD_HOST or QD_DEVICE");
     QD_CUDA(cudaMemcpyAsync(r->psi, in, r->esize * r->N,
                             where == QD_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, r->stream));
+    r->measured = false;  // a new input state starts a new circuit
+    return QD_OK;
+}
+
+int qd_ket_list(qd_reg *r, int32_t method, double threshold, int64_t cap, int64_t *indices, double *values,
+                int64_t *count) {
+    if (int rc = reg_ok(r)) return rc;
+    if (method != QD_OUT_AMPLITUDE && method != QD_OUT_PROBABILITY) return fail(QD_ERR_ARG, "unknown output method");
+    if (!count || cap < 0 || (cap > 0 && (!indices || !values))) return fail(QD_ERR_ARG, "bad output arguments");
+    if (!(threshold >= 0.0)) return fail(QD_ERR_ARG, "threshold must be >= 0");
+    const uint64_t nch = ket_chunks((uint64_t)r->N);
+    const size_t per = method == QD_OUT_AMPLITUDE ? 2 : 1;
+    int64_t *counts = nullptr, *idx_dev = nullptr;
+    double *val_dev = nullptr;
+    int rc = QD_OK;
+    if (cudaMalloc(&counts, sizeof(int64_t) * (2 * nch + 1)) != cudaSuccess) return fail(QD_ERR_OOM, "ket scratch");
+    if (cap > 0 && (cudaMalloc(&idx_dev, sizeof(int64_t) * cap) != cudaSuccess ||
+                    cudaMalloc(&val_dev, sizeof(double) * per * cap) != cudaSuccess))
+        rc = fail(QD_ERR_OOM, "ket output buffers");
+    int64_t total = 0;
+    if (rc == QD_OK) {
+        int64_t *offsets = counts + nch;
+        cudaError_t e = ket_select(r->psi, r->prec, (uint64_t)r->N, threshold, method == QD_OUT_AMPLITUDE ? 0 : 1,
+                                   cap, counts, offsets, idx_dev, val_dev, r->sm_count, r->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&total, offsets + nch, sizeof(int64_t), cudaMemcpyDeviceToHost, r->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
+        const int64_t n = total < cap ? total : cap;
+        if (e == cudaSuccess && n > 0)
+            e = cudaMemcpy(indices, idx_dev, sizeof(int64_t) * n, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && n > 0) e = cudaMemcpy(values, val_dev, sizeof(double) * per * n, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) rc = cuda_fail(e, "ket readout");
+    }
+    if (counts) cudaFree(counts);
+    if (idx_dev) cudaFree(idx_dev);
+    if (val_dev) cudaFree(val_dev);
+    if (rc == QD_OK) *count = total;
+    return rc;
+}
+
+int qd_run_moments(qd_reg *r, const qd_gate *gates, int32_t ngates, int32_t *n_moments) {
+    if (int rc = reg_ok(r)) return rc;
+    if (ngates < 0 || (ngates > 0 && !gates)) return fail(QD_ERR_ARG, "bad gate list");
+    if (r->N > kKronMaxN || r->n > kKronMaxQudits)
+        return fail(QD_ERR_DIM, "the moment path keeps N x N operators: registers of at most 4096 amplitudes");
+    if (r->measured) {
+        if (n_moments) *n_moments = 0;
+        return QD_OK;
+    }
+    std::vector<FuseGate> fg;
+    std::vector<const qd_gate *> orig;
+    if (int rc = collect_gates(r, gates, ngates, fg, orig)) return rc;
+    int nm = 0;
+    cudaError_t e = run_moments(r->psi, r->prec, r->N, r->n, r->dims, fg, &nm, r->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "moment path");
+    if (has_measure(gates, ngates)) r->measured = true;
+    if (n_moments) *n_moments = nm;
+    return QD_OK;
+}
+
+int qd_apply_toffoli(qd_reg *r, int32_t c1, int32_t carrier, int32_t t, int32_t shift) {
+    if (int rc = reg_ok(r)) return rc;
+    qd_gate g[3];
+    if (int rc = qd_toffoli_gates(r->dims, r->n, c1, carrier, t, shift, g)) return rc;
+    for (const qd_gate &x : g)
+        if (int rc = apply_record(r, &x)) return rc;
+    return QD_OK;
+}
+
+int qd_apply_mct_tree(qd_reg *r, const int32_t *controls, const int32_t *ctrl_levels, int32_t nc, int32_t t,
+                      int32_t shift) {
+    if (int rc = reg_ok(r)) return rc;
+    int32_t count = 0;
+    if (int rc = qd_mct_tree_gates(r->dims, r->n, controls, ctrl_levels, nc, t, shift, nullptr, 0, &count, nullptr))
+        return rc;
+    std::vector<qd_gate> g((size_t)count);
+    if (int rc = qd_mct_tree_gates(r->dims, r->n, controls, ctrl_levels, nc, t, shift, g.data(), count, &count,
+                                   nullptr))
+        return rc;
+    for (const qd_gate &x : g)
+        if (int rc = apply_record(r, &x)) return rc;
     return QD_OK;
 }
 
@@ -1325,6 +1578,7 @@ int qd_sync(qd_reg *r, int32_t *device_error) {
     QD_CUDA(cudaMemcpyAsync(&err, r->dev_err, sizeof(int32_t), cudaMemcpyDeviceToHost, r->stream));
     QD_CUDA(cudaStreamSynchronize(r->stream));
     if (device_error) *device_error = err;
+    if (err == 1) return fail(QD_ERR_TIMEOUT, "a bounded device wait of the tensor-core kernel expired");
     if (err) return fail(QD_ERR_DEVICE, "device error word set: " + std::to_string(err));
     return QD_OK;
 }
@@ -1411,6 +1665,26 @@ int host_register(const int32_t *dims, int32_t n, int32_t precision, qd_reg &r) 
 }
 }  // namespace
 
+int qd_moment_packing(const int32_t *dims, int32_t n, const qd_gate *gates, int32_t ngates, int32_t *moment_of_gate,
+                      int32_t *n_moments) {
+    qd_reg r;
+    if (int rc = host_register(dims, n, QD_C128, r)) return rc;
+    if (ngates < 0 || (ngates > 0 && !gates)) return fail(QD_ERR_ARG, "bad gate list");
+    std::vector<FuseGate> fg;
+    std::vector<const qd_gate *> orig;
+    if (int rc = collect_gates(&r, gates, ngates, fg, orig)) return rc;
+    int nm = 0;
+    const std::vector<int> m = pack_moments(n, fg, &nm);
+    // identity gates were dropped: report -1 for them, the moment otherwise
+    if (moment_of_gate) {
+        for (int i = 0; i < ngates; ++i) moment_of_gate[i] = -1;
+        for (size_t k = 0; k < orig.size(); ++k) moment_of_gate[orig[k] - gates] = m[k];
+    }
+    if (n_moments) *n_moments = nm;
+    return QD_OK;
+}
+
+
 int qd_debug_fuse_plan(const int32_t *dims, int32_t n, int32_t precision, const qd_gate *gates, int32_t ngates,
                        int32_t plan_kind, int32_t kmax, int32_t dmax, int32_t *seg_first, int32_t *seg_last,
                        int32_t cap, int32_t *nseg, double *model_cost) {
@@ -1422,7 +1696,8 @@ int qd_debug_fuse_plan(const int32_t *dims, int32_t n, int32_t precision, const 
     std::vector<const qd_gate *> orig;
     if (int rc = collect_gates(&r, gates, ngates, fg, orig)) return rc;
     std::vector<std::pair<int, int>> segs;
-    if (int rc = segments_for(&r, fg, plan_kind, segs, model_cost)) return rc;
+    std::vector<int> kinds;
+    if (int rc = segments_for(&r, fg, plan_kind, segs, kinds, model_cost)) return rc;
     for (size_t i = 0; i < segs.size() && (int32_t)i < cap; ++i) {
         if (seg_first) seg_first[i] = segs[i].first;
         if (seg_last) seg_last[i] = segs[i].second;
@@ -1439,7 +1714,7 @@ int qd_debug_segment_cost(const int32_t *dims, int32_t n, int32_t precision, con
     std::vector<const qd_gate *> orig;
     if (int rc = collect_gates(&r, gates, ngates, fg, orig)) return rc;
     if (first < 0 || last < first || last >= (int)fg.size() || !cost) return fail(QD_ERR_ARG, "bad segment");
-    *cost = segment_cost(fg, first, last, shape_of(&r), cost_for(&r, QD_PLAN_GREEDY));
+    *cost = segment_cost(fg, first, last, shape_of(&r), cost_for(&r, QD_PLAN_GREEDY), r.fuse_kmax);
     return QD_OK;
 }
 
@@ -1484,6 +1759,7 @@ struct qd_batch {
     uint32_t small_amps = 2048;
     uint64_t group_amps = uint64_t(1) << 25;
     uint32_t tiles_per_item = 1;
+    uint32_t poll_limit = kBatchPollLimit;
     uint32_t tile_cap = 0;
     uint32_t desc_bytes = kBatchDescBytes;
     double alg_bytes = 0;
@@ -1836,6 +2112,7 @@ int batch_store(qd_batch *b, int32_t c, const qd_gate *gates, int32_t ngates) {
     for (int i = 0; i < ngates; ++i) {
         qd_batch::Stored st;
         const qd_gate *gt = &gates[i];
+        if (gt->kind == QD_GATE_MEASURE) break;  // gates after the measurement flag are ignored (Sec. 3.4)
         int rc = validate(&r, gt->targets, gt->k, gt->controls, gt->ctrl_levels, gt->nc, st.a);
         if (!rc) rc = gate_matrix(&r, gt, st.a, st.M, &st.diag);
         GatePlan g;
@@ -1905,6 +2182,7 @@ BatchLaunch batch_desc(const qd_batch *b) {
     L.ctas_per_sm = b->ctas_per_sm;
     L.tile_cap = b->tile_cap;
     L.desc_bytes = b->desc_bytes;
+    L.poll_limit = b->poll_limit;
     return L;
 }
 
@@ -1977,6 +2255,14 @@ int qd_batch_tune(qd_batch *b, int32_t key, int64_t value) {
             if (value < 1 || value > 4096) return fail(QD_ERR_ARG, "tiles per item out of range");
             b->tiles_per_item = (uint32_t)value;
             break;
+        case QD_BATCH_POLL_LIMIT:
+            if (value < 0 || value > (int64_t(1) << 30)) return fail(QD_ERR_ARG, "poll limit out of range");
+            b->poll_limit = (uint32_t)value;
+            if (b->exec) {  // a new kernel argument: capture the graph again
+                cudaGraphExecDestroy(b->exec);
+                b->exec = nullptr;
+            }
+            return QD_OK;
         default:
             return fail(QD_ERR_ARG, "unknown batch tuning key");
     }
@@ -2054,6 +2340,19 @@ int qd_batch_info(qd_batch *b, int64_t *total, int32_t *items, int32_t *launches
         QD_CUDA(cudaStreamSynchronize(b->stream));
         *device_error = e;
     }
+    return QD_OK;
+}
+
+int qd_batch_sync(qd_batch *b, int32_t *device_error) {
+    if (!b) return fail(QD_ERR_ARG, "null batch");
+    int32_t e = 0;
+    if (b->derr) {
+        QD_CUDA(cudaMemcpyAsync(&e, b->derr, sizeof(int32_t), cudaMemcpyDeviceToHost, b->stream));
+        QD_CUDA(cudaStreamSynchronize(b->stream));
+    }
+    if (device_error) *device_error = e;
+    if (e == 2) return fail(QD_ERR_TIMEOUT, "a work item's bounded wait on its circuit counter expired");
+    if (e) return fail(QD_ERR_DEVICE, "batch device error word set: " + std::to_string(e));
     return QD_OK;
 }
 

@@ -164,13 +164,28 @@ struct MonoTileArgs {
 
 // Groups per thread per iteration: loads of all of them are issued before any
 // arithmetic, for memory-level parallelism (bounded by register pressure).
+// A permutation or diagonal gate moves few amplitudes per group (a qubit
+// phase touches one), so its kernel takes more groups per iteration.
 template <typename T, typename I, int MD>
 __host__ __device__ constexpr int direct_unroll() {
-    return (MD * (int)sizeof(v2<T>)) <= 32 && sizeof(I) == 4 ? 2 : 1;
+    return (MD * (int)sizeof(v2<T>)) <= 32 ? 2 : 1;
+}
+template <typename T, typename I, int MD>
+__host__ __device__ constexpr int mono_unroll() {
+    return MD <= 4 ? 2 : 1;
+}
+// Resident CTAs of 256 threads the register budget must allow (the memory
+// parallelism of these kernels is the loads all their threads have in
+// flight): for complex64, 4 (64 registers) where that costs no spills, 3 for
+// the 8- and 9-member dense kernels and the largest mono bucket, 2 for the
+// largest dense; complex128 (bound by FP64 arithmetic) is left unconstrained.
+template <typename T, int MD, bool DENSE>
+__host__ __device__ constexpr int direct_min_blocks() {
+    return !kSplit<T> ? 1 : MD >= 32 ? (DENSE ? 2 : 3) : (DENSE && (MD == 8 || MD == 9) ? 3 : 4);
 }
 
 template <typename T, typename I, int MD, bool EX>
-__global__ void __launch_bounds__(256) k_dense_direct(const __grid_constant__ DenseDirectArgs<T, I, MD> a) {
+__global__ void __launch_bounds__(256, (direct_min_blocks<T, MD, true>())) k_dense_direct(const __grid_constant__ DenseDirectArgs<T, I, MD> a) {
     constexpr int UN = direct_unroll<T, I, MD>();
     const int D = EX ? MD : a.D;
     const I step = (I)gridDim.x * blockDim.x;
@@ -242,8 +257,8 @@ __global__ void __launch_bounds__(256) k_dense_direct(const __grid_constant__ De
 }
 
 template <typename T, typename I, int MD>
-__global__ void __launch_bounds__(256) k_mono_direct(const __grid_constant__ MonoDirectArgs<T, I, MD> a) {
-    constexpr int UN = direct_unroll<T, I, MD>();
+__global__ void __launch_bounds__(256, (direct_min_blocks<T, MD, false>())) k_mono_direct(const __grid_constant__ MonoDirectArgs<T, I, MD> a) {
+    constexpr int UN = mono_unroll<T, I, MD>();
     const I step = (I)gridDim.x * blockDim.x;
     for (I r0 = (I)blockIdx.x * blockDim.x + threadIdx.x; r0 < a.R; r0 += UN * step) {
         I base[UN];

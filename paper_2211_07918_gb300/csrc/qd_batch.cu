@@ -35,7 +35,6 @@ namespace qd {
 namespace {
 
 constexpr int kBThreads = 128;
-constexpr uint32_t kPollLimit = 1u << 22;  // bounded waits on a circuit counter (>= 0.5 s)
 
 // Copy a descriptor from global to shared memory (word by word, all threads).
 template <typename T>
@@ -365,7 +364,7 @@ __global__ void __launch_bounds__(kBThreads, 5)
             const BChunk *__restrict__ chunks, const BGate *__restrict__ gates, const float2 *__restrict__ coef,
             const uint32_t *__restrict__ hofftab, const BItem *__restrict__ items, int32_t nitems,
             uint32_t *__restrict__ next, uint32_t *__restrict__ done, int32_t *__restrict__ err,
-            uint32_t desc_bytes) {
+            uint32_t desc_bytes, uint32_t poll_limit) {
     extern __shared__ __align__(16) unsigned char smraw[];
     BSeg &S = *reinterpret_cast<BSeg *>(smraw);
     unsigned char *desc = smraw + ((sizeof(BSeg) + 15) / 16) * 16;
@@ -387,7 +386,7 @@ __global__ void __launch_bounds__(kBThreads, 5)
             const volatile uint32_t *d = done + it.circuit;
             uint32_t polls = 0;
             while (*d < it.wait_target) {
-                if (++polls > kPollLimit) {
+                if (++polls > poll_limit) {
                     atomicExch(err, 2);
                     s_ok = 0;
                     break;
@@ -479,6 +478,8 @@ int batch_occupancy(uint32_t tile_cap, uint32_t desc_bytes) {
 cudaError_t batch_launch(const BatchLaunch &b, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1) {
     cudaError_t e = cudaMemsetAsync(b.counters, 0, sizeof(uint32_t) * (1 + (size_t)b.ncirc), s);
     if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(b.err, 0, sizeof(int32_t), s);  // the error word reports this run only
+    if (e != cudaSuccess) return e;
     k_batch_init<<<b.sm_count * 4, 256, 0, s>>>(b.arena, b.total);
     k_batch_ones<<<(b.ncirc + 255) / 256, 256, 0, s>>>(b.arena, b.offs, b.basis, b.ncirc);
     if (b.nitems > 0) {
@@ -488,7 +489,7 @@ cudaError_t batch_launch(const BatchLaunch &b, cudaStream_t s, cudaEvent_t ev0, 
         const int grid = b.sm_count * per_sm;
         if (ev0) cudaEventRecord(ev0, s);
         k_batch<<<grid, kBThreads, smem, s>>>(b.arena, b.offs, b.segs, b.chunks, b.gates, b.coef, b.hoff, b.items,
-                                             b.nitems, b.counters, b.counters + 1, b.err, b.desc_bytes);
+                                             b.nitems, b.counters, b.counters + 1, b.err, b.desc_bytes, b.poll_limit);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         if (ev1) cudaEventRecord(ev1, s);

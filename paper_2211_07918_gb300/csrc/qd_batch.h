@@ -108,7 +108,10 @@ struct BatchLaunch {
     int ctas_per_sm;     // 0: as many as fit
     uint32_t tile_cap;   // largest tile of any segment (shared-memory amplitudes)
     uint32_t desc_bytes; // shared-memory area for one chunk (>= every chunk, multiple of 16)
+    uint32_t poll_limit; // polls of a dependent item's wait before it gives up (error word 2)
 };
+
+constexpr uint32_t kBatchPollLimit = 1u << 22;  // default: >= 0.5 s of polling
 
 size_t batch_smem_bytes(uint32_t tile_cap, uint32_t desc_bytes);
 // Enqueue: reset the counters and every state to its basis state, the

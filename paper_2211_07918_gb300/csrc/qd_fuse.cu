@@ -149,21 +149,64 @@ LaunchFeatures launch_features(const RegisterShape &reg, const std::vector<int> 
     return lf;
 }
 
+int block_kernels(const RegisterShape &reg, int64_t D, int nq, int kmax, bool all_mono, bool all_diag, int *kinds) {
+    if (all_diag && (nq > kmax || D > kMonoBlockMaxD)) {
+        kinds[0] = kKernelDiagTable;
+        return 1;
+    }
+    if (all_mono && D <= kMonoBlockMaxD) {
+        kinds[0] = kKernelMono;
+        return 1;
+    }
+    if (reg.precision != 1) {
+        kinds[0] = kKernelBlock;
+        return 1;
+    }
+    if (D > kDenseBlockMaxD) {
+        kinds[0] = kKernelBlockTc;
+        return 1;
+    }
+    if (reg.tc_min_d == 0 && D >= kTcMinBlockD) {
+        kinds[0] = kKernelBlock;
+        kinds[1] = kKernelBlockTc;
+        return 2;
+    }
+    kinds[0] = (reg.tc_min_d > 0 && D >= reg.tc_min_d) ? kKernelBlockTc : kKernelBlock;
+    return 1;
+}
+
+uint64_t diag_table_size(const RegisterShape &reg, const std::vector<int> &qudits) {
+    int lo = reg.n, hi = -1;
+    for (int q : qudits) {
+        lo = std::min(lo, q);
+        hi = std::max(hi, q);
+    }
+    uint64_t T = 1;
+    for (int q = lo; q <= hi; ++q) {
+        T *= (uint64_t)reg.dims[q];
+        if (T > kDiagRunMaxTable) return kDiagRunMaxTable + 1;
+    }
+    return T;
+}
+
 double analytic_cost(const RegisterShape &reg, const LaunchFeatures &lf) {
     const double D = std::exp2((double)lf.f[0]);
     const bool c128 = lf.f[9] > 0.5f;
     const bool dense = lf.f[10] > 0.5f;
-    const bool block = lf.f[10] > 1.5f;
+    const bool block = lf.f[10] > 2.5f && lf.f[10] < 3.5f;  // fused block on the tensor cores
+    const bool table = lf.f[10] > 3.5f;                    // diagonal run through a table
     const double touched = (double)reg.N * std::exp2((double)lf.f[11]);
     const double b = c128 ? 16.0 : 8.0;
-    const double t_mem = 2.0 * touched * b / 5.0e12;
-    double t_cmp = 0.0;
-    if (dense) {
-        if (!c128 && block && D >= 9) {
-            // fused block on the tensor cores: 4 split-BF16 products of
-            // (2 Dp) x (2 Dp) per group, about 1.2 PFLOP/s usable
-            const double Dp = std::ceil(D / 8.0) * 8.0;
-            t_cmp = touched * 32.0 * Dp * Dp / D / 1.2e15;
+    double t_mem = 2.0 * touched * b / 5.0e12;
+    if (table) t_mem += std::exp2((double)lf.f[0]) * 16.0 / 5.0e12;
+    double t_cmp = table ? touched * 40.0 / 2.0e13 : 0.0;  // index arithmetic per amplitude
+    if (dense && !table) {
+        if (!c128 && block) {
+            // fused block on the tensor cores: 6 exact BF16 slice products of
+            // (2 Dp) x (2 Dp) per group; measured on GB300 the kernel moves
+            // about 3.5 TB/s at D = Dp, less in proportion to the padding
+            const double Dp = D <= 32 ? std::ceil(D / 8.0) * 8.0 : std::ceil(D / 16.0) * 16.0;
+            t_cmp = 2.0 * touched * b / (3.5e12 * D / Dp);
         } else {
             // complex64 with hi+lo coefficients: 8 D FFMA per amplitude plus
             // index work; complex128: 4 D DFMA per amplitude
@@ -174,7 +217,7 @@ double analytic_cost(const RegisterShape &reg, const LaunchFeatures &lf) {
 }
 
 double segment_cost(const std::vector<FuseGate> &gates, int first, int last, const RegisterShape &reg,
-                    const CostFn &cost) {
+                    const CostFn &cost, int kmax, int *kind_out) {
     if (first == last) {
         const FuseGate &g = gates[first];
         double frac = 1.0;
@@ -183,22 +226,45 @@ double segment_cost(const std::vector<FuseGate> &gates, int first, int last, con
             frac /= reg.dims[g.acting[m]];
             Dt /= reg.dims[g.acting[m]];
         }
+        if (kind_out) *kind_out = g.mono ? kKernelMono : kKernelDense;
         return cost(launch_features(reg, g.acting, Dt, g.mono ? kKernelMono : kKernelDense, frac));
     }
     const std::vector<int> s = union_qudits(gates, first, last);
-    const int D = (int)dim_of(s, reg.dims);
+    const int64_t D = dim_of(s, reg.dims);
     // a product of permutations with phases is one: it runs on the mono
     // kernel (up to its 32 local states), not as a dense block
-    bool all_mono = true;
-    for (int i = first; i <= last; ++i) all_mono = all_mono && gates[i].mono;
-    return cost(launch_features(reg, s, D, all_mono && D <= kMonoBlockMaxD ? kKernelMono : kKernelBlock, 1.0));
+    bool all_mono = true, all_diag = true;
+    for (int i = first; i <= last; ++i) {
+        all_mono = all_mono && gates[i].mono;
+        all_diag = all_diag && gates[i].diag;
+    }
+    int kinds[2];
+    const int nk = block_kernels(reg, D, (int)s.size(), kmax, all_mono, all_diag, kinds);
+    double best = 0.0;
+    for (int k = 0; k < nk; ++k) {
+        const int kind = kinds[k];
+        const double c = kind == kKernelDiagTable
+                             ? cost(launch_features(reg, s, (int)diag_table_size(reg, s), kind, 1.0))
+                             : cost(launch_features(reg, s, (int)D, kind, 1.0));
+        if (k == 0 || c < best) {
+            best = c;
+            if (kind_out) *kind_out = kind;
+        }
+    }
+    return best;
 }
 
 namespace {
+// A multi-gate segment is feasible as a block within the qudit and dimension
+// limits, and as a diagonal run (every gate diagonal) on any number of qudits
+// whose covering range gives a table of at most kDiagRunMaxTable entries.
 bool feasible(const std::vector<FuseGate> &gates, int first, int last, const RegisterShape &reg, int kmax,
               int Dmax) {
     if (first == last) return true;
     const std::vector<int> s = union_qudits(gates, first, last);
+    bool all_diag = true;
+    for (int i = first; i <= last && all_diag; ++i) all_diag = gates[i].diag;
+    if (all_diag && diag_table_size(reg, s) <= kDiagRunMaxTable) return true;
     return (int)s.size() <= kmax && dim_of(s, reg.dims) <= Dmax;
 }
 }  // namespace
@@ -210,8 +276,9 @@ std::vector<std::pair<int, int>> segment_greedy(const std::vector<FuseGate> &gat
     int start = 0;
     for (int i = 1; i <= n; ++i) {
         if (i < n && feasible(gates, start, i, reg, kmax, Dmax)) {
-            const double merged = segment_cost(gates, start, i, reg, cost);
-            const double split = segment_cost(gates, start, i - 1, reg, cost) + segment_cost(gates, i, i, reg, cost);
+            const double merged = segment_cost(gates, start, i, reg, cost, kmax);
+            const double split =
+                segment_cost(gates, start, i - 1, reg, cost, kmax) + segment_cost(gates, i, i, reg, cost, kmax);
             if (merged <= split) continue;
         }
         segs.push_back({start, i - 1});
@@ -229,7 +296,7 @@ std::vector<std::pair<int, int>> segment_exhaustive(const std::vector<FuseGate> 
     for (int i = 1; i <= n; ++i) {
         for (int j = i - 1; j >= 0; --j) {
             if (!feasible(gates, j, i - 1, reg, kmax, Dmax)) break;  // unions only grow as j decreases
-            const double c = best[j] + segment_cost(gates, j, i - 1, reg, cost);
+            const double c = best[j] + segment_cost(gates, j, i - 1, reg, cost, kmax);
             if (c < best[i]) {
                 best[i] = c;
                 from[i] = j;

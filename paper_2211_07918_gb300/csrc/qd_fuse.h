@@ -22,6 +22,7 @@ struct FuseGate {
     std::vector<double> M;  // Dact x Dact, interleaved complex, row-major
     int Dact = 1;
     bool mono = false;      // the original gate is a permutation with phases
+    bool diag = false;      // ... and its permutation is the identity (a diagonal gate)
     int nc = 0;             // number of controls in `acting`
 };
 
@@ -44,13 +45,34 @@ struct RegisterShape {
     const int64_t *strides;
     int64_t N;
     int precision;  // 1 = complex64, 2 = complex128
+    int tc_min_d;   // complex64 fused blocks with D >= tc_min_d (or D > 32) run on the tensor cores;
+                    // 0: the cost model chooses per block between the CUDA cores and the tensor cores
 };
 
 // Kernel kind of a launch (feature 10).
 constexpr int kKernelMono = 0;   // per-gate permutation with phases
 constexpr int kKernelDense = 1;  // per-gate dense (CUDA cores)
-constexpr int kKernelBlock = 2;  // fused block (tensor cores for complex64, D >= 9)
+constexpr int kKernelBlock = 2;    // fused block on the CUDA-core dense kernels (D <= 32)
+constexpr int kKernelBlockTc = 3;  // fused block on the tensor cores (complex64)
+constexpr int kKernelDiagTable = 4;  // run of diagonal gates applied through one table (any qudit count)
+constexpr uint64_t kDiagRunMaxTable = uint64_t(1) << 24;  // entries of a diagonal run's table
 constexpr int kMonoBlockMaxD = 32;  // a fused block of permutations with phases up to this D runs as mono
+constexpr int kDenseBlockMaxD = 32;  // largest fused block the CUDA-core dense kernels take
+
+// Candidate kernels of a fused (multi-gate) segment over nq qudits of
+// dimension D (written to kinds[], count returned): a diagonal table when
+// every gate is diagonal and the segment is beyond the block limits (more
+// than kmax qudits or D > kMonoBlockMaxD); mono when every gate is a
+// permutation with phases and D <= kMonoBlockMaxD; else dense on the CUDA
+// cores, or on the tensor cores for complex64 when D >= tc_min_d or D > 32.
+// With tc_min_d = 0 a complex64 dense block of kTcMinBlockD <= D <= 32 has
+// both dense kernels as candidates and the cost model picks the cheaper.
+constexpr int kTcMinBlockD = 9;
+int block_kernels(const RegisterShape &reg, int64_t D, int nq, int kmax, bool all_mono, bool all_diag, int *kinds);
+
+// Entries of the table of a diagonal run over `qudits`: the product of the
+// dimensions of the contiguous range [min, max] of those qudits.
+uint64_t diag_table_size(const RegisterShape &reg, const std::vector<int> &qudits);
 
 // Feature vector of a launch acting on `qudits` with target dimension D:
 // log2 D, qudit count, log2 of the (up to three) smallest strides, relative
@@ -78,8 +100,10 @@ std::vector<std::pair<int, int>> segment_greedy(const std::vector<FuseGate> &gat
 std::vector<std::pair<int, int>> segment_exhaustive(const std::vector<FuseGate> &gates, const RegisterShape &reg,
                                                     const CostFn &cost, int kmax, int Dmax, double *best_cost);
 
-// Cost the model assigns to one segment (single gate: its own kernel).
+// Cost the model assigns to one segment (single gate: its own kernel; a
+// block: its cheapest candidate kernel, returned in *kind if not NULL); kmax
+// is the block limit that decides between a mono block and a diagonal table.
 double segment_cost(const std::vector<FuseGate> &gates, int first, int last, const RegisterShape &reg,
-                    const CostFn &cost);
+                    const CostFn &cost, int kmax, int *kind = nullptr);
 
 }  // namespace qd

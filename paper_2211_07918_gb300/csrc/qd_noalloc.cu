@@ -38,13 +38,29 @@ static __device__ __align__(256) double g_noalloc_chunk_sums[kNoAllocChunkSums +
 
 int noalloc_fail(int code, const std::string &msg) { return qd::set_last_error(code, msg.c_str()); }
 
-// Device address of the scratch array on each device, looked up once per
-// device with that device current.  In host code the array's name stands for
-// a host-side shadow, not a device address, so it must never be handed to a
-// kernel directly.
+// Device address of the scratch array on each device, looked up with that
+// device current.  In host code the array's name stands for a host-side
+// shadow, not a device address, so it must never be handed to a kernel
+// directly.  Only a successful lookup is kept: a failed one (for example a
+// first call made during stream capture, or a transient error) is retried by
+// the next call instead of failing every later call on that device.
 double *g_scratch_ptr[kMaxDevices] = {};
-std::once_flag g_scratch_once[kMaxDevices];
-cudaError_t g_scratch_err[kMaxDevices] = {};
+std::mutex g_scratch_mu;
+
+cudaError_t scratch_for(int dev, double **out) {
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_ptr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_chunk_sums);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();  // reset the runtime's last-error state before a later retry
+            return e != cudaSuccess ? e : cudaErrorInvalidSymbol;
+        }
+        g_scratch_ptr[dev] = static_cast<double *>(p);
+    }
+    *out = g_scratch_ptr[dev];
+    return cudaSuccess;
+}
 
 }  // namespace
 
@@ -61,18 +77,15 @@ extern "C" int qd_cdf_noalloc(const void *state, int64_t n_amplitudes, int32_t p
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return noalloc_fail(QD_ERR_CUDA, std::string("qd_cdf_noalloc: ") + cudaGetErrorString(e));
     if (dev < 0 || dev >= kMaxDevices) return noalloc_fail(QD_ERR_ARG, "qd_cdf_noalloc: device ordinal too large");
-    std::call_once(g_scratch_once[dev], [dev] {
-        void *p = nullptr;
-        g_scratch_err[dev] = cudaGetSymbolAddress(&p, g_noalloc_chunk_sums);
-        g_scratch_ptr[dev] = g_scratch_err[dev] == cudaSuccess ? static_cast<double *>(p) : nullptr;
-    });
-    if (g_scratch_err[dev] != cudaSuccess || !g_scratch_ptr[dev])
+    double *scratch = nullptr;
+    e = scratch_for(dev, &scratch);
+    if (e != cudaSuccess)
         return noalloc_fail(QD_ERR_CUDA, std::string("qd_cdf_noalloc: cudaGetSymbolAddress failed: ") +
-                                             cudaGetErrorString(g_scratch_err[dev]));
+                                             cudaGetErrorString(e));
     // Every chunk-sum slot the scan reads is written earlier in the same call
     // (chunk sums, then their exclusive scan, then the per-chunk scans), so
     // what an earlier call left in the array is never read.
-    e = qd::cdf(state, precision, (uint64_t)n_amplitudes, g_scratch_ptr[dev], cdf_out,
+    e = qd::cdf(state, precision, (uint64_t)n_amplitudes, scratch, cdf_out,
                 static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return noalloc_fail(QD_ERR_CUDA, std::string("qd_cdf_noalloc: ") + cudaGetErrorString(e));
     return QD_OK;

@@ -8,7 +8,7 @@
 
 namespace qd {
 
-enum class Mode : int32_t { Direct = 0, Tile = 1, Tensor = 2 };
+enum class Mode : int32_t { Direct = 0, Tile = 1, Tensor = 2, Table = 3 };
 enum class Kind : int32_t { Dense = 0, Mono = 1 };
 
 // Largest number of amplitudes a tile-mode CTA stages in shared memory per
@@ -58,6 +58,11 @@ struct GatePlan {
     // --- tensor mode: fused block on tcgen05 (complex64 states) -------------
     int32_t Dp = 0;                    // D rounded up to a multiple of 8
     const void *tc_terms = nullptr;    // device: three BF16 terms of the real embedding
+    // --- table mode: a run of diagonal gates (psi[i] *= tab[(i / tab_div) mod tab_size])
+    uint64_t tab_div = 0;
+    uint64_t tab_size = 0;
+    const void *tab = nullptr;         // device table (float4 hi/lo or double2 entries)
+
     uint32_t active = 0;               // mono: bit i set if out[i] != in[i]
     uint32_t unit = 0;                 // mono: bit i set if lam[i] == 1 exactly
 

@@ -7,28 +7,33 @@
 // (128 x 2D reals, interleaved re/im), the update is one real GEMM
 //     Y (128 x 2D) = X (128 x 2D) * B^T,   B = [[Ur, -Ui], [Ui, Ur]] interleaved,
 // issued as tcgen05.mma kind::f16 (BF16 inputs, FP32 accumulation in TMEM)
-// with M = 128 groups and K = 2 Dp (Dp = D rounded up to a multiple of 8, or
-// of 16 above 32).  For Dp > 32 the N = 2 Dp outputs are computed in two
-// halves so that two accumulator slots fit in TMEM.
+// with M = 128 groups, K = 2 Dp and N = 2 Dp in one MMA pass (Dp = D rounded
+// up to a multiple of 8, or of 16 above 32).
 //
 // Precision.  The tensor cores round each accumulation step toward zero; a
-// rounded running sum loses on average about 0.36 ulp per instruction, always
-// toward zero, which shrinks every amplitude coherently (measured: 1 - F =
-// 1.5e-6 after one D = 64 block with a hi/lo split).  The kernel therefore
-// keeps every partial sum exact (the error-free splitting of Ozaki, Ogita,
-// Oishi and Rump, 2012): each state row r is scaled by 2^-e_r (e_r from the
-// row maximum) and cut into 8-bit fixed-point slices
+// rounded running sum of the whole product loses on average about 0.36 ulp
+// per instruction, always toward zero, which shrinks every amplitude
+// coherently (measured: 1 - F = 1.5e-6 after one D = 64 block with a hi/lo
+// split).  The kernel therefore keeps the leading part of every sum exact
+// (the error-free splitting of Ozaki, Ogita, Oishi and Rump, 2012): each
+// state row r is scaled by 2^-e_r (e_r from the row maximum) and cut into
+// 8-bit fixed-point slices
 //     x~ = x1 + x2 + x3 + O(2^-27),  x_s = k / 2^(9s-1),  |k| <= 256,
 // and each matrix row n likewise with its own 2^-f_n into B1 + B2 + B3.  Every
-// slice value is exact in BF16, every product of two slices is a multiple of
-// one quantum per significance level, and a level's sum stays below 2^24
-// quanta, so the tensor core accumulates it without rounding.  Three TMEM
-// accumulators hold the levels 2^0 (x1 B1), 2^-9 (x1 B2 + x2 B1) and 2^-18
-// (x1 B3 + x2 B2 + x3 B1); the epilogue adds them in FP32 with
-// round-to-nearest and rescales by 2^(e_r + f_n).  The matrix is represented
-// to 2^-27 (coherent error ~1e-8 per block); the dropped state terms are
-// incoherent, 2^-27 relative.
-//
+// slice value is exact in BF16 and every product x1 B1 is a multiple of
+// 2^-16 below 1, so the K = 2 Dp <= 128 products of the leading level sum to
+// fewer than 2^24 quanta and its accumulator (x1 B1) never rounds.  The
+// correction terms of significance 2^-9 and 2^-18 (x1 B2 + x2 B1 + x1 B3 +
+// x2 B2 + x3 B1) share a second accumulator.  That one does round toward zero,
+// but its value is itself a small correction whose sign is unrelated to the
+// output's, so the truncation is about 2^-32 of the output per instruction in
+// no preferred direction: no coherent shrink.  The epilogue adds the two
+// accumulators in FP32 with round-to-nearest and rescales by 2^(e_r + f_n).
+// The matrix is represented to 2^-27 (coherent error ~1e-8 per block); the
+// dropped state terms are incoherent, 2^-27 relative.  Two accumulators (not
+// one per significance level) leave room in the 512 TMEM columns for two
+// accumulator slots at every D up to 64.
+
 // Shared-memory operands use the no-swizzle K-major canonical layout: core
 // matrices of 8 rows x 16 bytes (8 BF16), consecutive along K at 128 B
 // (leading byte offset), 8-row groups at K*16 B (stride byte offset).
@@ -36,21 +41,22 @@
 // Warp roles (the steps of a tile overlap across tiles):
 //   producers (8 warps: two groups of 128 rows alternating tiles, or above
 //     D = 32 one group with two threads per row): gather a tile's groups,
-//     slice them into stage s of a shared-memory ring, arrive full[s];
-//   MMA issuer (warp 4, one lane): per output half h, wait full[s] and
-//     acc_empty[a], issue the slice products into accumulator slot a of a
-//     2-slot TMEM ring, commit to acc_full[a];
-//   epilogue (warps 0..3, one TMEM lane per thread): wait acc_full[a], combine
-//     the levels, scatter the outputs, arrive acc_empty[a].
+//     slice them in registers, then (once the stage is free) store the
+//     slices into stage s of a shared-memory ring and arrive full[s];
+//   MMA issuer (warp 4, one lane): wait full[s] and acc_empty[a], issue the
+//     slice products into accumulator slot a of a 2-slot TMEM ring, commit to
+//     acc_full[a];
+//   epilogue (warps 0..3, one TMEM lane per thread): wait acc_full[a], add the
+//     two accumulators, scatter the outputs, arrive acc_empty[a].
 // A stage is released by a tcgen05.commit to empty[s] once its MMAs have
 // completed, so producers fill the next tile while the epilogue drains the
 // previous one; the per-row scales of a tile travel to the epilogue through
 // their own 2-deep ring (sc_full / sc_empty), which keeps every barrier at
 // most one phase ahead of its waiters.
-// Unit u = (tile i, half h) uses slot u % 2; tile i uses stage i % STAGES;
-// mbarrier phases count the reuses.  Every wait is bounded and also gives up
-// when another warp has raised the abort flag (the device error word is set);
-// the MMA warp waits (bounded) for its last commit before TMEM is freed.
+// Tile i uses accumulator slot i % 2 and stage i % STAGES; mbarrier phases
+// count the reuses.  Every wait is bounded and also gives up when another
+// warp has raised the abort flag (the device error word is set); the MMA
+// warp waits (bounded) for its last commit before TMEM is freed.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -144,36 +150,19 @@ __device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t *r) {
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
 
-// 8-bit fixed-point slices of a value already scaled into [-1, 1]:
-// s1 = k1/2^8, s2 = k2/2^17, s3 = k3/2^26 with |k| <= 256 (exact in BF16).
-template <int XS>
-__device__ __forceinline__ void slices(float v, __nv_bfloat16 *out) {
-    const float s1 = rintf(v * 256.0f) * (1.0f / 256.0f);
-    const float r1 = v - s1;
-    const float s2 = rintf(r1 * 131072.0f) * (1.0f / 131072.0f);
-    out[0] = __float2bfloat16_rn(s1);
-    out[1] = __float2bfloat16_rn(s2);
-    if constexpr (XS == 3) {
-        const float r2 = r1 - s2;
-        out[2] = __float2bfloat16_rn(rintf(r2 * 67108864.0f) * (1.0f / 67108864.0f));
-    }
-}
-
 }  // namespace
 
 // Compile-time shape of the kernel for a bound MAXD on Dp.
 // Above Dp = 32 three state slices and the three matrix slices fill the
-// 227 KB of shared memory with one stage; the producers still load the next
-// tile into registers before they wait for that stage.  (Two state slices
-// would fit two stages, but the dropped 2^-18 residual changes the norm by a
-// random +-2^-18/sqrt(N) per block, visible on small registers.)
+// 227 KB of shared memory with one stage; the producers then load and slice
+// the next tile in registers before they wait for that stage, so only the
+// shared-memory stores sit between two tiles' MMAs.  (Two state slices would
+// fit two stages, but the dropped 2^-18 residual changes every amplitude by a
+// random +-2^-18 of its row maximum per block, visible on small registers.)
 template <int MAXD> struct TcCfg {
-    static constexpr int XS = 3;                        // state slices
-    static constexpr int NH = 1;                        // output parts (N = 2 Dp in one MMA pass)
-    // TMEM accumulator slots (3 levels x N columns each, 512 columns per SM):
-    // two above D = 32 would not fit, so there the next tile's MMAs wait for
-    // the epilogue to drain the single slot
-    static constexpr int SLOTS = MAXD <= 32 ? 2 : 1;
+    static constexpr int XS = 3;      // state slices
+    static constexpr int NACC = 2;    // accumulators per slot: exact leading level, corrections
+    static constexpr int SLOTS = 2;   // TMEM accumulator ring (2 x 2 x 2 Dp <= 512 columns)
     static constexpr int STAGES = MAXD <= 32 ? 3 : 1;   // shared-memory ring
     static constexpr int PW = 8;                        // producer warps
     // threads per tile row: above 32 amplitudes two threads share a row (32
@@ -182,7 +171,8 @@ template <int MAXD> struct TcCfg {
     static constexpr int NGRP = PW * 32 / (kTcRows * TPR);  // producer groups (alternate tiles)
     static constexpr int RA = MAXD / TPR;                   // amplitudes per producer thread
     static constexpr int THREADS = 32 * (5 + PW);
-    static constexpr int NPAIRS = XS == 3 ? 6 : 5;
+    static constexpr int NPAIRS = 6;
+    static constexpr bool PRE = MAXD <= 32;  // slices built before the stage is free
     // Stage-release barriers: tile i's MMAs commit to empty[i % NE]; the
     // writer of tile i waits for tile i - STAGES on empty[(i - STAGES) % NE].
     // With one stage NE = 2 (one barrier per tile parity): should two
@@ -206,19 +196,64 @@ struct TcArgs {
     int32_t *err;
 };
 
+// Packed FP32 pairs (Blackwell fma.rn.f32x2: two FMAs, each rounded as fmaf);
+// the (re, im) parts of an amplitude travel as one pair.
+typedef unsigned long long f2p;
+__device__ __forceinline__ f2p pk2(float a, float b) {
+    f2p r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ f2p fma2(f2p a, f2p b, f2p c) {
+    f2p d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+// BF16x2 word of a pair whose parts have at most 8 significant bits (exact):
+// the first part (re) in the low half, the second (im) in the high half.
+__device__ __forceinline__ uint32_t bf16x2_of(f2p x) {
+    float a, b;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(x));
+    uint32_t w;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(w) : "f"(b), "f"(a));
+    return w;
+}
+
+// The XS slices of one amplitude v = (re, im), already scaled into [-1, 1],
+// as BF16x2 words.  Level l rounds the remaining residual to a multiple of
+// q_l = 2^-(9l-1): with M = 1.5 * 2^23, fma(r, 1/q_l, M) - M is r / q_l
+// rounded to the nearest integer k (|r / q_l| < 2^22, so the sum's unit is
+// 1), the slice is k q_l and the next residual r - k q_l is exact (the two
+// are within a factor of two, or k = 0).
+template <int XS>
+__device__ __forceinline__ void slice_amp(f2p v, uint32_t *w) {
+    const float M = 12582912.0f;  // 1.5 * 2^23
+    const f2p Mp = pk2(M, M), Mn = pk2(-M, -M), one = pk2(1.f, 1.f), zero = 0ull;
+    f2p r = v;
+#pragma unroll
+    for (int l = 0; l < XS; ++l) {
+        const float inv_q = l == 0 ? 256.0f : (l == 1 ? 131072.0f : 67108864.0f);
+        const float q = 1.0f / inv_q;  // exact power of two
+        const f2p k = fma2(fma2(r, pk2(inv_q, inv_q), Mp), one, Mn);
+        const f2p sl = fma2(k, pk2(q, q), zero);
+        w[l] = bf16x2_of(sl);
+        if (l + 1 < XS) r = fma2(k, pk2(-q, -q), r);
+    }
+}
+
 template <typename I, int MAXD>
 __global__ void __launch_bounds__(TcCfg<MAXD>::THREADS, 1) k_block_tc(const __grid_constant__ TcArgs<I> a) {
     using C = TcCfg<MAXD>;
     extern __shared__ __align__(1024) unsigned char sm[];
     const uint32_t K = 2u * (uint32_t)a.Dp;
-    const uint32_t Nh = K / C::NH;  // output columns per half
+    const uint32_t Nc = K;  // output columns: N = 2 Dp reals
     const uint32_t xbytes = kTcRows * K * 2u;
     const uint32_t bbytes = K * K * 2u;
     unsigned char *B = sm;
     const float *bscale = reinterpret_cast<const float *>(B + 3u * bbytes);
     const uint32_t bregion = (3u * bbytes + K * 4u + 1023u) & ~1023u;
-    unsigned char *stages = sm + bregion;  // stage s: X1 | X2 (| X3) at s * XS * xbytes
-    __shared__ __align__(8) uint64_t full[C::STAGES], empty[C::NE], acc_full[2], acc_empty[2];
+    unsigned char *stages = sm + bregion;  // stage s: X1 | X2 | X3 at s * XS * xbytes
+    __shared__ __align__(8) uint64_t full[C::STAGES], empty[C::NE], acc_full[C::SLOTS], acc_empty[C::SLOTS];
     // row scales of a tile: a 2-deep ring between producers and epilogue
     __shared__ __align__(8) uint64_t sc_full[2], sc_empty[2];
     __shared__ int32_t erow[2][kTcRows];
@@ -228,7 +263,7 @@ __global__ void __launch_bounds__(TcCfg<MAXD>::THREADS, 1) k_block_tc(const __gr
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
     uint32_t ncols = 32;
-    while (ncols < (uint32_t)C::SLOTS * 3u * Nh) ncols <<= 1;
+    while (ncols < (uint32_t)(C::SLOTS * C::NACC) * Nc) ncols <<= 1;
 
     {
         const uint4 *src = reinterpret_cast<const uint4 *>(a.terms);
@@ -243,10 +278,12 @@ __global__ void __launch_bounds__(TcCfg<MAXD>::THREADS, 1) k_block_tc(const __gr
         // a stage is free once the MMAs reading it have completed (tcgen05.commit)
         for (int q = 0; q < C::NE; ++q)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&empty[q])) : "memory");
-        for (int q = 0; q < 2; ++q) {
+        for (int q = 0; q < C::SLOTS; ++q) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&acc_full[q])) : "memory");
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&acc_empty[q])), "r"(kTcRows)
                          : "memory");
+        }
+        for (int q = 0; q < 2; ++q) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&sc_full[q])), "r"(kTcRows)
                          : "memory");
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&sc_empty[q])), "r"(kTcRows)
@@ -293,23 +330,40 @@ __global__ void __launch_bounds__(TcCfg<MAXD>::THREADS, 1) k_block_tc(const __gr
             if constexpr (C::TPR == 2) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, 1));
             int e = 0;
             frexpf(amax, &e);  // amax <= 2^e
-            const float inv = ldexpf(1.0f, -e);
-            // row scale into the ring slot of this tile (the epilogue has read the
-            // scale of tile i - 2 from it)
-            const int es = (int)(i & 1);
-            const uint32_t euse = (uint32_t)(i >> 1);
-            // with two threads per row the warp leaves the loop together (the row
-            // maximum is exchanged by shuffles): every lane reaches the vote
-            bool ok = euse < 1 || ws_wait(smem_u32(&sc_empty[es]), (euse - 1) & 1u, &abort_flag, a.err);
-            if constexpr (C::TPR == 2) ok = __all_sync(0xffffffffu, ok);
-            if (!ok) break;
-            if (part == 0) {
-                erow[es][row] = e;
-                mbar_arrive(smem_u32(&sc_full[es]));
+            const f2p inv2 = pk2(ldexpf(1.0f, -e), ldexpf(1.0f, -e));
+            // up to D = 32 the slices are built in registers before the stage is
+            // free (word [s][j]: slice s of amplitude j0 + j); above, where one
+            // thread holds 32 amplitudes and the registers would not hold both,
+            // they are built chunk by chunk as they are stored
+            uint32_t w[C::PRE ? C::XS : 1][C::PRE ? C::RA : 1];
+            if constexpr (C::PRE) {
+#pragma unroll
+                for (int j = 0; j < C::RA; ++j) {
+                    uint32_t ws[3];
+                    slice_amp<C::XS>(fma2(pk2(v[j].x, v[j].y), inv2, 0ull), ws);
+#pragma unroll
+                    for (int s2 = 0; s2 < C::XS; ++s2) w[s2][j] = ws[s2];
+                }
             }
+            // row scale into the ring slot of this tile (the epilogue has read
+            // the scale of tile i - 2 from it)
+            {
+                const int es = (int)(i & 1);
+                const uint32_t euse = (uint32_t)(i >> 1);
+                // with two threads per row the warp leaves the loop together (the
+                // row maximum is exchanged by shuffles): every lane reaches the vote
+                bool ok = euse < 1 || ws_wait(smem_u32(&sc_empty[es]), (euse - 1) & 1u, &abort_flag, a.err);
+                if constexpr (C::TPR == 2) ok = __all_sync(0xffffffffu, ok);
+                if (!ok) break;
+                if (part == 0) {
+                    erow[es][row] = e;
+                    mbar_arrive(smem_u32(&sc_full[es]));
+                }
+            }
+            bool ok = true;
             if (i >= (I)C::STAGES) {
-                const I w = i - (I)C::STAGES;  // the tile whose MMAs last read this stage
-                ok = ws_wait(smem_u32(&empty[(int)(w % C::NE)]), (uint32_t)(w / C::NE) & 1u, &abort_flag, a.err);
+                const I wt = i - (I)C::STAGES;  // the tile whose MMAs last read this stage
+                ok = ws_wait(smem_u32(&empty[(int)(wt % C::NE)]), (uint32_t)(wt / C::NE) & 1u, &abort_flag, a.err);
             }
             if constexpr (C::TPR == 2) ok = __all_sync(0xffffffffu, ok);
             if (!ok) break;
@@ -317,22 +371,24 @@ __global__ void __launch_bounds__(TcCfg<MAXD>::THREADS, 1) k_block_tc(const __gr
 #pragma unroll
             for (int c0 = 0; c0 < C::RA; c0 += 4) {  // 4 amplitudes = 8 BF16 = one 16-byte chunk per slice
                 if (j0 + c0 < a.Dp) {
-                    __align__(16) __nv_bfloat16 h[C::XS][8];
+                    const uint32_t o = cm_off((uint32_t)row, (uint32_t)(2 * (j0 + c0)), K);
+                    uint32_t q[C::XS][4];
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
-                        __nv_bfloat16 sr[3], si[3];
-                        slices<C::XS>(v[c0 + u].x * inv, sr);
-                        slices<C::XS>(v[c0 + u].y * inv, si);
+                        if constexpr (C::PRE) {
 #pragma unroll
-                        for (int q = 0; q < C::XS; ++q) {
-                            h[q][2 * u] = sr[q];
-                            h[q][2 * u + 1] = si[q];
+                            for (int s2 = 0; s2 < C::XS; ++s2) q[s2][u] = w[s2][c0 + u];
+                        } else {
+                            uint32_t ws[3];
+                            slice_amp<C::XS>(fma2(pk2(v[c0 + u].x, v[c0 + u].y), inv2, 0ull), ws);
+#pragma unroll
+                            for (int s2 = 0; s2 < C::XS; ++s2) q[s2][u] = ws[s2];
                         }
                     }
-                    const uint32_t o = cm_off((uint32_t)row, (uint32_t)(2 * (j0 + c0)), K);
 #pragma unroll
-                    for (int q = 0; q < C::XS; ++q)
-                        *reinterpret_cast<uint4 *>(X + (uint32_t)q * xbytes + o) = *reinterpret_cast<const uint4 *>(h[q]);
+                    for (int s2 = 0; s2 < C::XS; ++s2)
+                        *reinterpret_cast<uint4 *>(X + (uint32_t)s2 * xbytes + o) =
+                            make_uint4(q[s2][0], q[s2][1], q[s2][2], q[s2][3]);
                 }
             }
             asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
@@ -341,48 +397,42 @@ __global__ void __launch_bounds__(TcCfg<MAXD>::THREADS, 1) k_block_tc(const __gr
     } else if (warp == 4) {
         // ------------------------------------------------------------ MMA issuer
         if ((tid & 31) == 0) {
-            const uint32_t idesc = idesc_bf16(kTcRows, Nh);
+            const uint32_t idesc = idesc_bf16(kTcRows, Nc);
             const uint32_t lbo = 128u, sbo = K * 16u;
             const uint32_t b0 = smem_u32(B);
-            // (level, x slice, B slice); the first pair of each level starts its accumulator
-            const int pairs[6][3] = {{0, 0, 0}, {1, 0, 1}, {1, 1, 0}, {2, 0, 2}, {2, 1, 1}, {2, 2, 0}};
+            // (accumulator, x slice, B slice): the exact leading level x1 B1, then
+            // every correction pair into the second accumulator; the first pair of
+            // each accumulator starts it
+            const int pairs[6][3] = {{0, 0, 0}, {1, 0, 1}, {1, 1, 0}, {1, 0, 2}, {1, 1, 1}, {1, 2, 0}};
             const uint32_t ksteps = K / 16u;
             I issued = 0, released = 0;
             for (I i = 0; i < nlocal; ++i) {
                 const int st = (int)(i % C::STAGES);
                 if (!ws_wait(smem_u32(&full[st]), (uint32_t)(i / C::STAGES) & 1u, &abort_flag, a.err)) break;
+                const int sl = (int)(i % C::SLOTS);
+                if (i >= (I)C::SLOTS &&
+                    !ws_wait(smem_u32(&acc_empty[sl]), (uint32_t)(i / C::SLOTS - 1) & 1u, &abort_flag, a.err))
+                    break;
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                 const uint32_t x0 = smem_u32(stages + (uint32_t)st * C::XS * xbytes);
-                bool stop = false;
-                for (int h = 0; h < C::NH; ++h) {
-                    const I u = i * C::NH + h;
-                    const int sl = (int)(u % C::SLOTS);
-                    if (u >= (I)C::SLOTS && !ws_wait(smem_u32(&acc_empty[sl]), (uint32_t)(u / C::SLOTS - 1) & 1u,
-                                                       &abort_flag, a.err)) {
-                        stop = true;
-                        break;
-                    }
-                    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                    const uint32_t acc = tmem + (uint32_t)sl * 3u * Nh;
-                    const uint32_t bhalf = (uint32_t)h * (Nh / 8u) * sbo;  // first output row of this half
-                    // the pair table is unrolled into constants; a K step moves both
-                    // operands by 256 bytes, i.e. 16 in the descriptors' address field
-                    // (shared addresses stay below 2^18, so the field does not overflow)
+                const uint32_t acc = tmem + (uint32_t)sl * (uint32_t)C::NACC * Nc;
+                // the pair table is unrolled into constants; a K step moves both
+                // operands by 256 bytes, i.e. 16 in the descriptors' address field
+                // (shared addresses stay below 2^18, so the field does not overflow)
 #pragma unroll
-                    for (int pp = 0; pp < C::NPAIRS; ++pp) {
-                        const uint32_t dcol = acc + (uint32_t)pairs[pp][0] * Nh;
-                        const uint32_t xa = x0 + (uint32_t)pairs[pp][1] * xbytes;
-                        const uint32_t bt = b0 + (uint32_t)pairs[pp][2] * bbytes + bhalf;
-                        const bool first_of_level = (pp == 0 || pp == 1 || pp == 3);
-                        const uint64_t da = smem_desc(xa, lbo, sbo), db = smem_desc(bt, lbo, sbo);
-                        mma_bf16(dcol, da, db, idesc, first_of_level ? 0u : 1u);
+                for (int pp = 0; pp < C::NPAIRS; ++pp) {
+                    const uint32_t dcol = acc + (uint32_t)pairs[pp][0] * Nc;
+                    const uint32_t xa = x0 + (uint32_t)pairs[pp][1] * xbytes;
+                    const uint32_t bt = b0 + (uint32_t)pairs[pp][2] * bbytes;
+                    const bool first_of_acc = (pp == 0 || pp == 1);
+                    const uint64_t da = smem_desc(xa, lbo, sbo), db = smem_desc(bt, lbo, sbo);
+                    mma_bf16(dcol, da, db, idesc, first_of_acc ? 0u : 1u);
 #pragma unroll 1
-                        for (uint32_t ks = 1; ks < ksteps; ++ks)
-                            mma_bf16(dcol, da + (uint64_t)(ks * 16u), db + (uint64_t)(ks * 16u), idesc, 1u);
-                    }
-                    mma_commit(smem_u32(&acc_full[sl]));
-                    issued = u + 1;
+                    for (uint32_t ks = 1; ks < ksteps; ++ks)
+                        mma_bf16(dcol, da + (uint64_t)(ks * 16u), db + (uint64_t)(ks * 16u), idesc, 1u);
                 }
-                if (stop) break;
+                mma_commit(smem_u32(&acc_full[sl]));
+                issued = i + 1;
                 mma_commit(smem_u32(&empty[(int)(i % C::NE)]));  // the stage is free once these MMAs complete
                 released = i + 1;
             }
@@ -403,8 +453,7 @@ __global__ void __launch_bounds__(TcCfg<MAXD>::THREADS, 1) k_block_tc(const __gr
         }
     } else {
         // ------------------------------------------------------------ epilogue
-        const int row = tid;         // TMEM lane of this thread (warps 0..3)
-        const int Dh = (int)Nh / 2;  // amplitudes per half
+        const int row = tid;  // TMEM lane of this thread (warps 0..3)
         for (I i = 0; i < nlocal; ++i) {
             // the producers' row scale of this tile
             const int es = (int)(i & 1);
@@ -416,48 +465,35 @@ __global__ void __launch_bounds__(TcCfg<MAXD>::THREADS, 1) k_block_tc(const __gr
             const I g = t * kTcRows + row;
             const bool valid = g < a.R;
             const I base = valid ? expand(g, a.ex) : 0;
-            bool stop = false;
-            for (int h = 0; h < C::NH; ++h) {
-                const I u = i * C::NH + h;
-                const int sl = (int)(u % C::SLOTS);
-                if (!ws_wait(smem_u32(&acc_full[sl]), (uint32_t)(u / C::SLOTS) & 1u, &abort_flag, a.err)) {
-                    stop = true;
-                    break;
-                }
-                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                const uint32_t lane_addr = tmem + (uint32_t)sl * 3u * Nh + ((uint32_t)(warp * 32) << 16);
-                const int j0 = h * Dh;
+            const int sl = (int)(i % C::SLOTS);
+            if (!ws_wait(smem_u32(&acc_full[sl]), (uint32_t)(i / C::SLOTS) & 1u, &abort_flag, a.err)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const uint32_t lane_addr = tmem + (uint32_t)sl * (uint32_t)C::NACC * Nc + ((uint32_t)(warp * 32) << 16);
 #pragma unroll
-                for (int c0 = 0; c0 < MAXD / C::NH; c0 += 8) {  // 8 amplitudes = 16 columns per level
-                    if (c0 < Dh) {
-                        uint32_t l0[16], l1[16], l2[16];
-                        tmem_ld16_nowait(lane_addr + (uint32_t)(2 * c0), l0);
-                        tmem_ld16_nowait(lane_addr + Nh + (uint32_t)(2 * c0), l1);
-                        tmem_ld16_nowait(lane_addr + 2u * Nh + (uint32_t)(2 * c0), l2);
-                        tmem_wait_ld();
-                        if (valid) {
+            for (int c0 = 0; c0 < MAXD; c0 += 8) {  // 8 amplitudes = 16 columns per accumulator
+                if (c0 < a.Dp) {
+                    uint32_t l0[16], l1[16];
+                    tmem_ld16_nowait(lane_addr + (uint32_t)(2 * c0), l0);
+                    tmem_ld16_nowait(lane_addr + Nc + (uint32_t)(2 * c0), l1);
+                    tmem_wait_ld();
+                    if (valid) {
 #pragma unroll
-                            for (int uu = 0; uu < 8; ++uu) {
-                                const int j = j0 + c0 + uu;
-                                if (j < a.D) {
-                                    const int n = 2 * j;
-                                    const float re = (__uint_as_float(l0[2 * uu]) +
-                                                      (__uint_as_float(l1[2 * uu]) + __uint_as_float(l2[2 * uu]))) *
-                                                     (escale * bscale[n]);
-                                    const float im =
-                                        (__uint_as_float(l0[2 * uu + 1]) +
-                                         (__uint_as_float(l1[2 * uu + 1]) + __uint_as_float(l2[2 * uu + 1]))) *
-                                        (escale * bscale[n + 1]);
-                                    a.psi[base + a.off[j]] = make_float2(re, im);
-                                }
+                        for (int uu = 0; uu < 8; ++uu) {
+                            const int j = c0 + uu;
+                            if (j < a.D) {
+                                const int n = 2 * j;
+                                const float re = (__uint_as_float(l0[2 * uu]) + __uint_as_float(l1[2 * uu])) *
+                                                 (escale * bscale[n]);
+                                const float im = (__uint_as_float(l0[2 * uu + 1]) + __uint_as_float(l1[2 * uu + 1])) *
+                                                 (escale * bscale[n + 1]);
+                                a.psi[base + a.off[j]] = make_float2(re, im);
                             }
                         }
                     }
                 }
-                asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-                mbar_arrive(smem_u32(&acc_empty[sl]));
             }
-            if (stop) break;
+            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+            mbar_arrive(smem_u32(&acc_empty[sl]));
         }
     }
     __syncthreads();
@@ -553,9 +589,9 @@ static cudaError_t launch_tc_im(const GatePlan &g, void *psi, int sm_count, int3
     if (e != cudaSuccess) return e;
     int occ = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, C::THREADS, smem);
-    // TMEM: 512 columns per SM; each CTA holds the next power of two >= slots * 3 levels * N/NH
+    // TMEM: 512 columns per SM; each CTA holds the next power of two >= slots * accumulators * N
     int ncols = 32;
-    while (ncols < C::SLOTS * 3 * 2 * g.Dp / C::NH) ncols <<= 1;
+    while (ncols < C::SLOTS * C::NACC * 2 * g.Dp) ncols <<= 1;
     const int tmem_cap = 512 / ncols;
     occ = occ < 1 ? 1 : (occ > tmem_cap ? tmem_cap : occ);
     const uint64_t tiles = (g.R + kTcRows - 1) / kTcRows;

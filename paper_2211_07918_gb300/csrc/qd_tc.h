@@ -8,7 +8,7 @@
 
 namespace qd {
 
-// Smallest and largest block dimension the tensor-core kernel takes.
+// Smallest and largest block dimension the tensor-core kernel is used for.
 constexpr int kTcMinD = 9;
 constexpr int kTcMaxD = 64;
 

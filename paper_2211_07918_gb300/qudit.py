@@ -19,13 +19,14 @@ from .build import LIB_PATH
 QD_OK = 0
 QD_C64, QD_C128 = 1, 2
 QD_HOST, QD_DEVICE = 0, 1
-QD_GATE_X, QD_GATE_Z, QD_GATE_H, QD_GATE_U, QD_GATE_DIAG = 1, 2, 3, 4, 5
+QD_GATE_X, QD_GATE_Z, QD_GATE_H, QD_GATE_U, QD_GATE_DIAG, QD_GATE_MEASURE = 1, 2, 3, 4, 5, 6
+QD_OUT_AMPLITUDE, QD_OUT_PROBABILITY = 0, 1
 QD_PLAN_NONE, QD_PLAN_GREEDY, QD_PLAN_LEARNED, QD_PLAN_EXHAUSTIVE = 0, 1, 2, 3
 QD_MAX_TARGETS, QD_MAX_CONTROLS = 6, 8
-QD_TUNE_TILE_STRIDE, QD_TUNE_FUSE_KMAX, QD_TUNE_FUSE_DMAX = 1, 2, 3
+QD_TUNE_TILE_STRIDE, QD_TUNE_FUSE_KMAX, QD_TUNE_FUSE_DMAX, QD_TUNE_TC_MIN_D = 1, 2, 3, 4
 QD_MODEL_FEATURES, QD_MODEL_PARAMS = 12, 9217
 QD_BATCH_TILE_AMPS, QD_BATCH_CTAS_PER_SM, QD_BATCH_SMALL_AMPS, QD_BATCH_GROUP_AMPS = 1, 2, 3, 4
-QD_BATCH_TILES_PER_ITEM = 5
+QD_BATCH_TILES_PER_ITEM, QD_BATCH_POLL_LIMIT = 5, 6
 ERRORS = {-1: "QD_ERR_ARG", -2: "QD_ERR_DIM", -3: "QD_ERR_OVERLAP", -4: "QD_ERR_OOM", -5: "QD_ERR_CUDA",
           -6: "QD_ERR_TIMEOUT", -7: "QD_ERR_DEVICE", -8: "QD_ERR_UNSUPPORTED"}
 
@@ -111,6 +112,18 @@ _SIGS = {
     "qd_batch_timings": [_vp, ctypes.POINTER(ctypes.c_float), _dp],
     "qd_batch_autotune": [_vp, _i32, _i64p, ctypes.POINTER(ctypes.c_float)],
     "qd_batch_destroy": [_vp],
+    "qd_batch_sync": [_vp, _i32p],
+    "qd_measure_all": [_vp],
+    "qd_is_measured": [_vp, _i32p],
+    "qd_toffoli_gates": [_i32p, _i32, _i32, _i32, _i32, _i32, ctypes.POINTER(QdGate)],
+    "qd_apply_toffoli": [_vp, _i32, _i32, _i32, _i32],
+    "qd_mct_tree_gates": [_i32p, _i32, _i32p, _i32p, _i32, _i32, _i32, ctypes.POINTER(QdGate), _i32, _i32p, _i32p],
+    "qd_apply_mct_tree": [_vp, _i32p, _i32p, _i32, _i32, _i32],
+    "qd_ket_list": [_vp, _i32, ctypes.c_double, _i64, _i64p, _dp, _i64p],
+    "qd_ket_label": [_i32p, _i32, _i64, ctypes.c_char_p, _i32],
+    "qd_qasm_parse": [ctypes.c_char_p, _i32p, _i32, _i32p, ctypes.POINTER(QdGate), _i32, _i32p, _i32p],
+    "qd_run_moments": [_vp, ctypes.POINTER(QdGate), _i32, _i32p],
+    "qd_moment_packing": [_i32p, _i32, ctypes.POINTER(QdGate), _i32, _i32p, _i32p],
 }
 
 
@@ -229,7 +242,9 @@ def qd_apply_mct(reg: int, controls, t: int, shift: int = 1, ctrl_levels=None) -
     _check(load().qd_apply_mct(_vp(reg), cp, lp, len(c), t, shift))
 
 
-_KIND = {"X": QD_GATE_X, "Z": QD_GATE_Z, "H": QD_GATE_H, "U": QD_GATE_U, "DIAG": QD_GATE_DIAG}
+_KIND = {"X": QD_GATE_X, "Z": QD_GATE_Z, "H": QD_GATE_H, "U": QD_GATE_U, "DIAG": QD_GATE_DIAG,
+         "MEASURE": QD_GATE_MEASURE}
+_KIND_NAME = {v: k for k, v in _KIND.items()}
 
 
 class GateArray:
@@ -292,7 +307,8 @@ def qd_plan_profile(plan: int, enable: bool = True) -> None:
     _check(load().qd_plan_profile(_vp(plan), 1 if enable else 0))
 
 
-KCLASS_NAMES = {0: "dense_direct", 1: "dense_tile", 2: "mono_direct", 3: "mono_tile", 4: "tensor_block"}
+KCLASS_NAMES = {0: "dense_direct", 1: "dense_tile", 2: "mono_direct", 3: "mono_tile", 4: "tensor_block",
+                5: "diag_table"}
 
 
 def qd_plan_timings(plan: int, with_times: bool = True):
@@ -353,7 +369,10 @@ def qd_marginal(reg: int, q: int, d: int) -> np.ndarray:
     return out
 
 
-def qd_cdf(reg: int, out: Optional[np.ndarray] = None) -> np.ndarray:
+def qd_cdf(reg: int, out: Optional[np.ndarray] = None, where: int = QD_HOST, dev_ptr: int = 0):
+    if where == QD_DEVICE:
+        _check(load().qd_cdf(_vp(reg), ctypes.cast(_vp(dev_ptr), _dp), QD_DEVICE))
+        return None
     if out is None:
         out = np.empty(_n(reg), dtype=np.float64)
     _check(load().qd_cdf(_vp(reg), out.ctypes.data_as(_dp), QD_HOST))
@@ -719,3 +738,195 @@ def qd_batch_autotune(batch: int, reps: int = 2) -> dict:
 
 def qd_batch_destroy(batch: int) -> None:
     _check(load().qd_batch_destroy(_vp(batch)))
+
+
+# ---- circuit layer: measurement flag, Toffoli / MCT decompositions, ket
+# readout, QuDiet QASM, the paper's moment execution model -----------------
+
+def _gate_from_struct(st):
+    """A workloads.Gate view of one qd_gate record (named gates only)."""
+    from .workloads import Gate
+    ctrls = tuple(int(st.controls[i]) for i in range(st.nc))
+    levels = tuple(int(st.ctrl_levels[i]) for i in range(st.nc)) if st.nc else None
+    return Gate(_KIND_NAME[int(st.kind)], tuple(int(st.targets[i]) for i in range(st.k)), ctrls, levels,
+                int(st.param))
+
+
+def qd_measure_all(reg: int) -> None:
+    _check(load().qd_measure_all(_vp(reg)))
+
+
+def qd_is_measured(reg: int) -> bool:
+    v = _i32()
+    _check(load().qd_is_measured(_vp(reg), ctypes.byref(v)))
+    return bool(v.value)
+
+
+def qd_toffoli_gates(dims: Sequence[int], c1: int, carrier: int, t: int, shift: int = 1) -> list:
+    d, dp = _arr_i32(dims)
+    out = (QdGate * 3)()
+    _check(load().qd_toffoli_gates(dp, len(d), c1, carrier, t, shift, out))
+    return [_gate_from_struct(out[i]) for i in range(3)]
+
+
+def qd_apply_toffoli(reg: int, c1: int, carrier: int, t: int, shift: int = 1) -> None:
+    _check(load().qd_apply_toffoli(_vp(reg), c1, carrier, t, shift))
+
+
+def qd_mct_tree_gates(dims: Sequence[int], controls, t: int, shift: int = 1, ctrl_levels=None):
+    """(gate list, depth) of the logarithmic-depth MCT decomposition."""
+    d, dp = _arr_i32(dims)
+    c, cp = _arr_i32(controls)
+    lv, lp = _arr_i32(ctrl_levels) if ctrl_levels is not None else (None, None)
+    cnt, depth = _i32(), _i32()
+    _check(load().qd_mct_tree_gates(dp, len(d), cp, lp, len(c), t, shift, None, 0, ctypes.byref(cnt), None))
+    out = (QdGate * max(1, cnt.value))()
+    _check(load().qd_mct_tree_gates(dp, len(d), cp, lp, len(c), t, shift, out, cnt.value, ctypes.byref(cnt),
+                                    ctypes.byref(depth)))
+    return [_gate_from_struct(out[i]) for i in range(cnt.value)], depth.value
+
+
+def qd_apply_mct_tree(reg: int, controls, t: int, shift: int = 1, ctrl_levels=None) -> None:
+    c, cp = _arr_i32(controls)
+    lv, lp = _arr_i32(ctrl_levels) if ctrl_levels is not None else (None, None)
+    _check(load().qd_apply_mct_tree(_vp(reg), cp, lp, len(c), t, shift))
+
+
+def qd_ket_list(reg: int, method: int = QD_OUT_AMPLITUDE, threshold: float = 1e-14, cap: Optional[int] = None):
+    """(indices int64[m], values) of the basis states with |psi_i|^2 > threshold,
+    ascending; values complex128[m] (amplitudes) or float64[m] (probabilities);
+    m = min(total, cap); also returns the total."""
+    if cap is None:
+        cnt = _i64()
+        _check(load().qd_ket_list(_vp(reg), method, threshold, 0, None, None, ctypes.byref(cnt)))
+        cap = cnt.value
+    idx = np.zeros(max(cap, 1), dtype=np.int64)
+    per = 2 if method == QD_OUT_AMPLITUDE else 1
+    val = np.zeros(max(cap, 1) * per, dtype=np.float64)
+    cnt = _i64()
+    _check(load().qd_ket_list(_vp(reg), method, threshold, cap, idx.ctypes.data_as(_i64p), val.ctypes.data_as(_dp),
+                              ctypes.byref(cnt)))
+    m = min(cnt.value, cap)
+    vals = val[: 2 * m].view(np.complex128) if per == 2 else val[:m]
+    return idx[:m], vals.copy(), cnt.value
+
+
+def qd_ket_label(dims: Sequence[int], index: int) -> str:
+    d, dp = _arr_i32(dims)
+    buf = ctypes.create_string_buffer(4 * len(d) + 8)
+    _check(load().qd_ket_label(dp, len(d), int(index), buf, len(buf)))
+    return buf.value.decode()
+
+
+def ket_dict(reg: int, dims: Sequence[int], method: int = QD_OUT_AMPLITUDE, threshold: float = 1e-14) -> dict:
+    """OutputType.print: {ket label: amplitude or probability} of the kept
+    basis states (labels qudit 0 first), from qd_ket_list / qd_ket_label."""
+    idx, vals, _ = qd_ket_list(reg, method, threshold)
+    return {qd_ket_label(dims, int(i)): (complex(v) if method == QD_OUT_AMPLITUDE else float(v))
+            for i, v in zip(idx, vals)}
+
+
+def output(reg: int, dims: Sequence[int], output_type: str = "print", method: str = "probability"):
+    """The paper's OutputType ("print": ket dict; "state": the raw state
+    array) and OutputMethod ("amplitude" or "probability")."""
+    m = QD_OUT_AMPLITUDE if method == "amplitude" else QD_OUT_PROBABILITY
+    if output_type == "state":
+        return qd_get_amplitudes(reg) if m == QD_OUT_AMPLITUDE else qd_probabilities(reg)
+    return ket_dict(reg, dims, m)
+
+
+def qd_qasm_parse(text: str):
+    """(dims, gate list) of a QuDiet QASM program; raises QuditError with the
+    line number on a syntax error."""
+    src = text.encode()
+    n, ng, line = _i32(), _i32(), _i32()
+    rc = load().qd_qasm_parse(src, None, 0, ctypes.byref(n), None, 0, ctypes.byref(ng), ctypes.byref(line))
+    if rc != QD_OK:
+        err = QuditError(rc, load().qd_last_error().decode(errors="replace"))
+        err.line = line.value
+        raise err
+    dims = np.zeros(max(n.value, 1), dtype=np.int32)
+    arr = (QdGate * max(ng.value, 1))()
+    _check(load().qd_qasm_parse(src, dims.ctypes.data_as(_i32p), n.value, ctypes.byref(n), arr, ng.value,
+                                ctypes.byref(ng), ctypes.byref(line)))
+    return [int(x) for x in dims[: n.value]], [_gate_from_struct(arr[i]) for i in range(ng.value)]
+
+
+def qd_run_moments(reg: int, gates) -> int:
+    """Apply the gates through the paper's moment / Kronecker / GEMM-chain
+    execution model; returns the moment count."""
+    ga = gates if isinstance(gates, GateArray) else GateArray(gates)
+    nm = _i32()
+    _check(load().qd_run_moments(_vp(reg), ga.ptr, ga.n, ctypes.byref(nm)))
+    return nm.value
+
+
+def qd_moment_packing(dims: Sequence[int], gates):
+    d, dp = _arr_i32(dims)
+    ga = gates if isinstance(gates, GateArray) else GateArray(gates)
+    m = np.zeros(max(ga.n, 1), dtype=np.int32)
+    nm = _i32()
+    _check(load().qd_moment_packing(dp, len(d), ga.ptr, ga.n, m.ctypes.data_as(_i32p), ctypes.byref(nm)))
+    return m[: ga.n], nm.value
+
+
+class Circuit:
+    """Circuit builder over the C ABI (the paper's qc.h / qc.x / qc.cx /
+    qc.Toffoli / measure_all calls, Sec. 3.4 and 3.6): collects gate records;
+    the decompositions come from the library (qd_toffoli_gates,
+    qd_mct_tree_gates); run() prepares and runs them on a register."""
+
+    def __init__(self, dims: Sequence[int]):
+        from .workloads import Gate
+        self._Gate = Gate
+        self.dims = [int(d) for d in dims]
+        self.gates = []
+
+    def x(self, q, plus=1):
+        self.gates.append(self._Gate("X", (q,), param=plus))
+        return self
+
+    def z(self, q, power=1):
+        self.gates.append(self._Gate("Z", (q,), param=power))
+        return self
+
+    def h(self, q):
+        self.gates.append(self._Gate("H", (q,)))
+        return self
+
+    def cx(self, qs, plus=1, level=None):
+        c, t = qs
+        self.gates.append(self._Gate("X", (t,), (c,), None if level is None else (level,), plus))
+        return self
+
+    def unitary(self, targets, matrix, controls=(), levels=None):
+        self.gates.append(self._Gate("U", tuple(targets), tuple(controls), levels, 0, np.asarray(matrix)))
+        return self
+
+    def toffoli(self, qs, plus=1):
+        c1, carrier, t = qs
+        self.gates.extend(qd_toffoli_gates(self.dims, c1, carrier, t, plus))
+        return self
+
+    def mct(self, controls, t, plus=1, levels=None):
+        self.gates.extend(qd_mct_tree_gates(self.dims, controls, t, plus, levels)[0])
+        return self
+
+    def measure_all(self):
+        self.gates.append(self._Gate("MEASURE", ()))
+        return self
+
+    def run(self, reg: int, plan_kind: int = QD_PLAN_NONE) -> None:
+        qd_run_circuit(reg, self.gates, plan_kind)
+
+
+def qd_batch_sync(batch: int) -> int:
+    """The last run's device error word; raises QuditError (QD_ERR_TIMEOUT for
+    an expired wait) when it is set."""
+    err = _i32()
+    rc = load().qd_batch_sync(_vp(batch), ctypes.byref(err))
+    if rc != QD_OK:
+        e = QuditError(rc, load().qd_last_error().decode(errors="replace"))
+        e.device_error = err.value
+        raise e
+    return err.value

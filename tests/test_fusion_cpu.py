@@ -130,3 +130,22 @@ def test_segment_of_permutations_is_costed_as_mono():
     c_single = L.qd_debug_segment_cost(dims, mono, 0, 0, L.QD_C128)
     assert c_mono < c_dense
     assert c_mono <= c_single * 1.0001
+
+
+def test_diagonal_runs_are_planned_as_single_segments():
+    """In the d-ary QFT the controlled phases onto one target (Sec. 2.1.2 phase
+    gates, controlled) form a run of diagonal gates; the exhaustive planner
+    takes each run, whatever its qudit count, as one segment, and every
+    segment it returns is either within the block limits or all-diagonal."""
+    dims, gates = wl.circuit_c2(n_qubits=3, n_ququarts=5)
+    segs, _ = L.qd_debug_fuse_plan(dims, gates, L.QD_PLAN_EXHAUSTIVE, L.QD_C64, 3, 64)
+    assert segs[0][0] == 0 and segs[-1][1] == len(gates) - 1
+    assert all(b + 1 == c for (_, b), (c, _) in zip(segs, segs[1:]))
+    long_diag = 0
+    for a, b in segs:
+        qs = {q for g in gates[a:b + 1] for q in tuple(g.targets) + tuple(g.controls or ())}
+        all_diag = all(g.kind in ("Z", "DIAG") for g in gates[a:b + 1])
+        if len(qs) > 3:
+            assert all_diag, (a, b)
+            long_diag += 1
+    assert long_diag >= 1

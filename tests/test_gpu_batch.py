@@ -224,3 +224,50 @@ def test_batch_c3_full():
                 check_circuit(d, g, L.qd_batch_get_amplitudes(b, c, N).astype(np.complex128), p)
     finally:
         L.qd_batch_destroy(b)
+
+
+@pytest.mark.parametrize("stream_kind", ["legacy", "captured"])
+def test_bounded_wait_expires_and_next_run_is_clean(stream_kind):
+    """A work item of a later segment waits (bounded) on its circuit's
+    completion counter.  With a poll limit of 0 every item whose segment
+    dependencies are not complete at its first look gives up: it skips its
+    tiles, the kernel still finishes, and the run reports error word 2 as
+    QD_ERR_TIMEOUT.  Back at the default limit the next run is clean and its
+    states match the oracle."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(4242)
+    dims = [3] * 12 + [2] * 2  # 2.1e6 amplitudes: thousands of 256-amplitude tiles per segment
+    gates = []
+    for a, b in [(0, 13), (6, 12), (3, 9), (1, 10), (2, 11), (4, 8), (5, 7), (0, 6)]:
+        # two-qudit gates on far-apart qudits: with 256-amplitude tiles every
+        # gate or two starts a new segment, whose items wait on the previous one
+        gates.append(wl.Gate("U", (a, b), matrix=wl.haar_unitary(dims[a] * dims[b], rng)))
+    circuits = [(dims, gates), ([2, 3, 2], [wl.Gate("H", (1,))])]
+    stream = torch.cuda.Stream().cuda_stream if stream_kind == "captured" else 0
+    b = L.qd_batch_create([d for d, _ in circuits], stream)
+    try:
+        L.qd_batch_tune(b, L.QD_BATCH_TILE_AMPS, 256)
+        for c, (_, g) in enumerate(circuits):
+            L.qd_batch_set_circuit(b, c, g)
+        assert L.qd_batch_info(b)["items"] > 4 * (int(np.prod(dims)) // 256)  # several segments
+        L.qd_batch_tune(b, L.QD_BATCH_POLL_LIMIT, 0)
+        L.qd_batch_run(b)
+        with pytest.raises(L.QuditError) as e:
+            L.qd_batch_sync(b)
+        assert e.value.code == -6 and e.value.device_error == 2
+        assert L.qd_batch_info(b, with_error=True)["device_error"] == 2
+        L.qd_batch_tune(b, L.QD_BATCH_POLL_LIMIT, 1 << 22)
+        L.qd_batch_run(b)
+        assert L.qd_batch_sync(b) == 0
+        N = int(np.prod(dims))
+        got = L.qd_batch_get_amplitudes(b, 0, N).astype(np.complex128)
+    finally:
+        L.qd_batch_destroy(b)
+    ref = qf.run_circuit(dims, gates)
+    assert np.max(np.abs(got - ref)) <= TOL64
+    small = L.qd_batch_create([[2]], 0)
+    try:
+        with pytest.raises(L.QuditError):
+            L.qd_batch_tune(small, L.QD_BATCH_POLL_LIMIT, -1)
+    finally:
+        L.qd_batch_destroy(small)

@@ -19,8 +19,10 @@ def _built():
     L.load()
 
 
-def _run(dims, gates, prec, kind, psi0=None, kmax=None, dmax=None):
+def _run(dims, gates, prec, kind, psi0=None, kmax=None, dmax=None, tc_min_d=None):
     with L.Register(dims, None, prec) as r:
+        if tc_min_d:
+            L.qd_set_tuning(r.h, L.QD_TUNE_TC_MIN_D, tc_min_d)
         if kmax:
             L.qd_set_tuning(r.h, L.QD_TUNE_FUSE_KMAX, kmax)
         if dmax:
@@ -90,8 +92,10 @@ def test_fused_c1_full_size(prec, kind, c1_ref):
     _check(psi, ref, prec)
 
 
-def _kclasses(dims, gates, prec, kind, kmax=3, dmax=None):
+def _kclasses(dims, gates, prec, kind, kmax=3, dmax=None, tc_min_d=None):
     with L.Register(dims, None, prec) as r:
+        if tc_min_d:
+            L.qd_set_tuning(r.h, L.QD_TUNE_TC_MIN_D, tc_min_d)
         L.qd_set_tuning(r.h, L.QD_TUNE_FUSE_KMAX, kmax)
         if dmax:
             L.qd_set_tuning(r.h, L.QD_TUNE_FUSE_DMAX, dmax)
@@ -131,9 +135,46 @@ def test_tensor_blocks_random(seed):
     psi0 = rng.standard_normal(N) + 1j * rng.standard_normal(N)
     psi0 /= np.linalg.norm(psi0)
     ref = qf.run_circuit(dims, gates, psi0=psi0)
-    for kind in (L.QD_PLAN_GREEDY, L.QD_PLAN_EXHAUSTIVE):
-        psi, info = _run(dims, gates, L.QD_C64, kind, psi0=psi0, kmax=3, dmax=64)
-        _check(psi, ref, L.QD_C64)
+    # default routing (the cost model picks per block), every block of D >= 9
+    # on the tensor cores, and every block of D <= 32 on the CUDA cores
+    for tc_min_d in (None, 9, 65):
+        for kind in (L.QD_PLAN_GREEDY, L.QD_PLAN_EXHAUSTIVE):
+            psi, info = _run(dims, gates, L.QD_C64, kind, psi0=psi0, kmax=3, dmax=64, tc_min_d=tc_min_d)
+            _check(psi, ref, L.QD_C64)
+
+
+def test_block_routing_threshold():
+    """Fused complex64 blocks below the threshold run on the CUDA-core dense
+    kernels, at or above it on the tensor cores; above 32 always on the
+    tensor cores; with threshold 0 the plan's cost model picks."""
+    rng = np.random.default_rng(8)
+    dims = [3, 3, 2, 4, 4, 4]
+    g27 = [wl.Gate("U", (0,), matrix=wl.haar_unitary(3, rng)), wl.Gate("U", (1,), matrix=wl.haar_unitary(3, rng)),
+           wl.Gate("U", (0, 2), matrix=wl.haar_unitary(6, rng))]  # qudits {0,1,2}: D = 18
+    g64 = [wl.Gate("U", (3, 4), matrix=wl.haar_unitary(16, rng)), wl.Gate("U", (5, 4), matrix=wl.haar_unitary(16, rng))]
+    segs = [(0, 2)]
+    with L.Register(dims, None, L.QD_C64) as r:
+        for tc, want18 in ((None, None), (9, "tensor_block_D18"), (19, "dense_direct_D18"),
+                           (18, "tensor_block_D18"), (65, "dense_direct_D18"), (0, None)):
+            if tc is not None:
+                L.qd_set_tuning(r.h, L.QD_TUNE_TC_MIN_D, tc)
+            plan = L.qd_plan_create_segmented(r.h, g27, segs)
+            names = [L.kclass_name(int(c)) for c in L.qd_plan_timings(plan, with_times=False)[2]]
+            L.qd_plan_destroy(plan)
+            if want18 is None:  # the cost model picks one of the two dense kernels
+                assert names in (["tensor_block_D18"], ["dense_direct_D18"]), (tc, names)
+            else:
+                assert names == [want18], (tc, names)
+            plan = L.qd_plan_create_segmented(r.h, g64, [(0, 1)])
+            names = [L.kclass_name(int(c)) for c in L.qd_plan_timings(plan, with_times=False)[2]]
+            L.qd_plan_destroy(plan)
+            assert names == ["tensor_block_D64"], (tc, names)
+        with pytest.raises(L.QuditError):
+            L.qd_set_tuning(r.h, L.QD_TUNE_TC_MIN_D, 8)
+        with pytest.raises(L.QuditError):
+            L.qd_set_tuning(r.h, L.QD_TUNE_TC_MIN_D, -1)
+        with pytest.raises(L.QuditError):
+            L.qd_set_tuning(r.h, L.QD_TUNE_TC_MIN_D, 66)
 
 
 @pytest.mark.parametrize("dims", [[4] * 13, [2] * 6 + [3] * 12])
@@ -157,6 +198,7 @@ def test_tensor_blocks_many_tiles_per_cta(dims):
             c = qs[2]
             gates.append(wl.Gate("U", (b, c), matrix=wl.haar_unitary(dims[b] * dims[c], rng)))
     with L.Register(dims, None, L.QD_C64) as fused, L.Register(dims, None, L.QD_C64) as ref:
+        L.qd_set_tuning(fused.h, L.QD_TUNE_TC_MIN_D, 9)  # every dense block of D >= 9 on the tensor cores
         plan = L.qd_plan_create(fused.h, gates, L.QD_PLAN_EXHAUSTIVE)
         classes = {L.kclass_name(int(c)) for c in L.qd_plan_timings(plan, with_times=False)[2]}
         L.qd_plan_run(plan)
@@ -189,9 +231,65 @@ def test_fused_permutation_blocks_run_as_mono(kind):
             c = int(rng.choice([q for q in range(len(dims)) if q != t]))
             gates.append(wl.Gate("X", (t,), (c,), (int(rng.integers(0, dims[c])),), int(rng.integers(1, dims[t]))))
     ref = qf.run_circuit(dims, gates)
-    psi, info = _run(dims, gates, L.QD_C64, kind)
+    psi, info = _run(dims, gates, L.QD_C64, kind, tc_min_d=9)
     _check(psi, ref, L.QD_C64)
     assert info["blocks"] > 0
-    classes = _kclasses(dims, gates, L.QD_C64, kind)
+    classes = _kclasses(dims, gates, L.QD_C64, kind, tc_min_d=9)
     assert not any(c.startswith("tensor_block") for c in classes), classes
     assert any(c.startswith("mono") and int(c.split("_D")[1]) >= 9 for c in classes), classes
+
+
+def _diag_heavy_circuit(dims, ngates, seed):
+    """Runs of diagonal gates (Z powers, random-phase diagonals on one or two
+    qudits, controlled phases) between dense and permutation gates."""
+    rng = np.random.default_rng(seed)
+    n = len(dims)
+    gates = []
+    for _ in range(ngates):
+        r = rng.random()
+        if r < 0.12:
+            q = int(rng.integers(0, n))
+            gates.append(wl.Gate("U", (q,), matrix=wl.haar_unitary(dims[q], rng)))
+        elif r < 0.18:
+            q = int(rng.integers(0, n))
+            gates.append(wl.Gate("X", (q,), param=int(rng.integers(1, dims[q]))))
+        elif r < 0.4:
+            q = int(rng.integers(0, n))
+            gates.append(wl.Gate("Z", (q,), param=int(rng.integers(1, dims[q]))))
+        elif r < 0.7:
+            a, b = (int(x) for x in rng.choice(n, size=2, replace=False))
+            D = dims[a] * dims[b]
+            gates.append(wl.Gate("DIAG", (a, b), matrix=np.exp(2j * np.pi * rng.random(D))))
+        else:
+            c, t = (int(x) for x in rng.choice(n, size=2, replace=False))
+            gates.append(wl.Gate("DIAG", (t,), (c,), (int(rng.integers(0, dims[c])),),
+                                 matrix=np.exp(2j * np.pi * rng.random(dims[t]))))
+    return gates
+
+
+@pytest.mark.parametrize("prec", [L.QD_C128, L.QD_C64])
+@pytest.mark.parametrize("case", ["qft", "diag0", "diag1"])
+def test_diagonal_runs_match_oracle(prec, case):
+    """Runs of consecutive diagonal gates beyond the block limits become one
+    table launch each (covered range starting at qudit 0 included, tables of
+    ragged mixed-radix size); the fused state equals the oracle's."""
+    if case == "qft":
+        dims, gates = wl.circuit_c2(n_qubits=3, n_ququarts=5)
+    else:
+        rng = np.random.default_rng(700 + int(case[-1]))
+        dims = [int(x) for x in rng.choice([2, 3, 4, 5], size=7)]
+        while qo.register_size(dims) > 40000:
+            dims.pop()
+        gates = _diag_heavy_circuit(dims, 60, 700 + int(case[-1]))
+    N = qo.register_size(dims)
+    rng = np.random.default_rng(3)
+    psi0 = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    psi0 /= np.linalg.norm(psi0)
+    ref = qf.run_circuit(dims, gates, psi0=psi0)
+    seen = set()
+    for kind in (L.QD_PLAN_GREEDY, L.QD_PLAN_EXHAUSTIVE):
+        psi, info = _run(dims, gates, prec, kind, psi0=psi0, kmax=3, dmax=64 if prec == L.QD_C64 else 32)
+        _check(psi, ref, prec)
+        seen.update(c.split("_D")[0] for c in _kclasses(dims, gates, prec, kind, 3,
+                                                      64 if prec == L.QD_C64 else 32))
+    assert "diag_table" in seen, seen
