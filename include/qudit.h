@@ -254,6 +254,7 @@ int qd_plan_destroy(qd_plan *plan);
 #define QD_KCLASS_MONO_TILE 3
 #define QD_KCLASS_TENSOR_BLOCK 4 /* fused block on tcgen05 (exact BF16 slices, FP32 accumulate) */
 #define QD_KCLASS_DIAG_TABLE 5   /* run of diagonal gates through one table (D = qudits the table covers) */
+#define QD_KCLASS_DENSE_TABLE 6  /* dense part followed by a diagonal run's table, one pass (D = dense part) */
 int qd_plan_profile(qd_plan *plan, int32_t enable);
 int qd_plan_timings(qd_plan *plan, float *ms, double *alg_bytes, int32_t *kclass);
 /* Plan, run once with direct launches (no graph capture) and release. */
@@ -430,18 +431,43 @@ int qd_model_grad_raw(qd_model *model, const float *Xn, const float *t, int32_t 
 /* Attach a model to a register for QD_PLAN_LEARNED (NULL detaches; the
  * model must outlive the plans made with it). */
 int qd_set_cost_model(qd_reg *reg, qd_model *model);
+/* Kernel forms of one launch (launch feature 10). */
+#define QD_FORM_MONO 0       /* one permutation / diagonal gate */
+#define QD_FORM_DENSE 1      /* one dense gate */
+#define QD_FORM_BLOCK 2      /* fused block, CUDA-core dense kernel (D <= 32) */
+#define QD_FORM_BLOCK_TC 3   /* fused block, tensor-core kernel (complex64, 9 <= D <= 64) */
+#define QD_FORM_DIAG_RUN 4   /* run of diagonal gates through one table */
+#define QD_FORM_DENSE_RUN 5  /* dense part (<= 16 states) followed by a diagonal run */
 /* The 12 launch features of gates[first..last] (indices of the non-identity
- * gates) as one launch on this register: log2 D, qudit count, log2 of the
- * three smallest strides, relative positions, log2 N, precision, kernel kind
- * (0 permutation/diagonal gate, 1 dense gate, 2 fused block), log2 of the
- * control-slice fraction. */
+ * gates) as one launch on this register, in the form that
+ * qd_plan_create_segmented gives that segment: log2 D (of the table, for a
+ * diagonal run), qudit count, log2 of the three smallest strides, relative
+ * positions, log2 N, precision, kernel form (QD_FORM_*), log2 of the
+ * control-slice fraction (of the table size, for a dense part + run).  Errors: QD_ERR_ARG (bad segment). */
 int qd_segment_features(qd_reg *reg, const qd_gate *gates, int32_t ngates, int32_t first, int32_t last, float *out);
+/* Every feasible kernel form of gates[first..last] under the hard limits of
+ * qd_plan_create_segmented (the candidates a planner weighs): *nforms of
+ * them (at most 3), kinds[i] the kernel form (QD_FORM_*) and features[i*12..] its 12
+ * launch features, for i < cap.  QD_ERR_OOM when *nforms > cap (the first
+ * cap are written). */
+int qd_segment_forms(qd_reg *reg, const qd_gate *gates, int32_t ngates, int32_t first, int32_t last, int32_t *kinds,
+                     float *features, int32_t cap, int32_t *nforms);
 /* A plan from an explicit segmentation: segment i covers the non-identity
  * gates [seg_first[i], seg_last[i]] (contiguous, in order, covering all);
  * multi-gate segments become fused blocks regardless of the size limits of
- * QD_TUNE_FUSE_*, up to 6 qudits and D <= 64 (complex64) or 32 (complex128). */
+ * QD_TUNE_FUSE_*, up to 6 qudits and D <= 64 (complex64) or 32 (complex128),
+ * or, when every gate of the segment is diagonal, one diagonal-run launch
+ * over any qudits whose covering range has at most 2^24 states, or, when the
+ * segment is a dense part of at most 16 states followed by such a run, one
+ * dense launch that applies the run's table to its outputs. */
 int qd_plan_create_segmented(qd_reg *reg, const qd_gate *gates, int32_t ngates, const int32_t *seg_first,
                              const int32_t *seg_last, int32_t nseg, qd_plan **out);
+/* qd_plan_create_segmented with the kernel form of every segment given:
+ * seg_kind[i] a kernel form from qd_segment_forms for that segment, or -1
+ * for the cost model's choice (seg_kind NULL: all -1).  Errors: QD_ERR_ARG
+ * when a given form is not feasible for its segment. */
+int qd_plan_create_forms(qd_reg *reg, const qd_gate *gates, int32_t ngates, const int32_t *seg_first,
+                         const int32_t *seg_last, const int32_t *seg_kind, int32_t nseg, qd_plan **out);
 
 /* ---- QuDiet QASM front end (Sec. 4) ----------------------------------- */
 /* Parse a QuDiet QASM program: ".qudit n"; n declarations "qudit NAME (d)" in

@@ -82,15 +82,32 @@ def random_diag_run(rng: np.random.Generator, dims: Sequence[int]):
     return out
 
 
+def random_dense_with_run(rng: np.random.Generator, dims: Sequence[int]):
+    """A dense gate on one or two qudits (at most 16 states) followed by a
+    diagonal run over 4-12 qudits: one dense launch with a table epilogue."""
+    n = len(dims)
+    for _ in range(50):
+        k = int(rng.integers(1, 3))
+        qs = [int(x) for x in rng.choice(n, size=k, replace=False)]
+        if int(np.prod([dims[q] for q in qs])) <= 16:
+            break
+    else:
+        qs = [0]
+    D = int(np.prod([dims[q] for q in qs]))
+    return [Gate("U", tuple(qs), matrix=wl.haar_unitary(D, rng))] + random_diag_run(rng, dims)
+
+
 def random_launch(rng: np.random.Generator, dims: Sequence[int], dmax: int = 64):
     """Gates that form one launch: a single permutation/diagonal gate, a
     single dense gate, a fused block of two dense gates over 2-3 qudits, a
-    fused block of 2-4 permutations with phases over 2-3 qudits, or a run of
-    diagonal gates over 4-12 qudits."""
+    fused block of 2-4 permutations with phases over 2-3 qudits, a run of
+    diagonal gates over 4-12 qudits, or a dense gate followed by such a run."""
     n = len(dims)
-    kind = rng.choice(["mono", "dense", "block", "block", "block", "monoblock", "diagrun"])
+    kind = rng.choice(["mono", "dense", "block", "block", "block", "monoblock", "diagrun", "denserun"])
     if kind == "diagrun":
         return random_diag_run(rng, dims)
+    if kind == "denserun":
+        return random_dense_with_run(rng, dims)
     if kind == "monoblock":
         # fused permutations with phases (shifts, clocks, controlled shifts)
         # on 2-3 qudits: the product runs on the mono kernel
@@ -155,10 +172,11 @@ def random_launch(rng: np.random.Generator, dims: Sequence[int], dmax: int = 64)
             Gate("U", (b, c), matrix=wl.haar_unitary(dims[b] * dims[c], rng))]
 
 
-def time_launch(reg: int, gates, reps: int = 3) -> float:
-    """Median device time (ms) of the single launch the gates form."""
+def time_launch(reg: int, gates, reps: int = 3, kind: int = -1) -> float:
+    """Median device time (ms) of the single launch the gates form (in the
+    given kernel form; -1: the analytic cost model's choice)."""
     ga = L.GateArray(gates)
-    plan = L.qd_plan_create_segmented(reg, ga, [(0, len(gates) - 1)])
+    plan = L.qd_plan_create_segmented(reg, ga, [(0, len(gates) - 1)], [kind])
     try:
         L.qd_plan_profile(plan, True)
         ts = []
@@ -186,14 +204,14 @@ def generate(n_samples: int, seed: int = 0, registers: Iterable[Sequence[int]] =
                 if len(y) >= n_samples:
                     break
                 gates = random_launch(rng, dims, 64 if precision == L.QD_C64 else 32)
-                # dense blocks of D <= 32 are timed on either kernel (the
-                # features record which), so that the model can price both
-                L.qd_set_tuning(h, L.QD_TUNE_TC_MIN_D, 9 if rng.random() < 0.5 else 65)
+                # every feasible form of the launch is timed (both block
+                # kernels for 9 <= D <= 32, a block or a dense part + run),
+                # each sample with the features of the form that ran
                 ga = L.GateArray(gates)
-                f = L.qd_segment_features(h, ga, 0, len(gates) - 1)
-                ms = time_launch(h, gates, reps)
-                X.append(f)
-                y.append(math.log(max(ms, 1e-4) * 1e3))
+                for kind, f in L.qd_segment_forms(h, ga, 0, len(gates) - 1):
+                    ms = time_launch(h, gates, reps, kind)
+                    X.append(f)
+                    y.append(math.log(max(ms, 1e-4) * 1e3))
         finally:
             L.qd_destroy(h)
         if log:
@@ -276,14 +294,36 @@ def _is_diag(g) -> bool:
     return g.kind in ("Z", "DIAG")
 
 
-def exhaustive_measured(reg: int, dims: Sequence[int], gates, kmax: int = 3, dmax: int = 64, reps: int = 3):
+def _dense_then_run(gates, dims, a, b, kmax):
+    """Gates a..b as a dense part (<= kmax qudits, <= 16 states) followed by a
+    nonempty run of diagonal gates whose covering range has <= 2^24 states."""
+    k = b
+    while k >= a and _is_diag(gates[k]):
+        k -= 1
+    if k < a or k == b:
+        return False
+    pre = set()
+    for g in gates[a:k + 1]:
+        pre |= set(g.controls or ()) | set(g.targets)
+    run = set()
+    for g in gates[k + 1:b + 1]:
+        run |= set(g.controls or ()) | set(g.targets)
+    return (len(pre) <= kmax and int(np.prod([dims[q] for q in pre])) <= 16
+            and int(np.prod(dims[min(run):max(run) + 1])) <= (1 << 24))
+
+
+def exhaustive_measured(reg: int, dims: Sequence[int], gates, kmax: int = 3, dmax: int = 64, reps: int = 3,
+                        record=None):
     """The measured optimum: the minimum-time contiguous segmentation, where every
     candidate segment's cost is its measured launch time (dynamic program
     over prefixes; a segment of several gates must span <= kmax qudits of
-    total dimension <= dmax, or be a run of diagonal gates whose covering
-    qudit range gives a table of <= 2^24 entries; a dense block of D <= 32 is
-    timed on the CUDA cores and on the tensor cores and the faster counts).
-    Returns (segments, summed measured ms)."""
+    total dimension <= dmax, be a run of diagonal gates whose covering qudit
+    range gives a table of <= 2^24 entries, or a dense part followed by such a
+    run; every feasible kernel form of a segment is timed -- a dense block of
+    9 <= D <= 32 on the CUDA cores and on the tensor cores, a block or a
+    dense part + run -- and the fastest counts).  record: a list that
+    receives (features, ms) of every timed form.  Returns (segments, summed
+    measured ms)."""
     n = len(gates)
     cost = {}
     best = [0.0] + [math.inf] * n
@@ -296,15 +336,17 @@ def exhaustive_measured(reg: int, dims: Sequence[int], gates, kmax: int = 3, dma
             all_diag = all_diag and _is_diag(gates[j])
             in_block = len(qs) <= kmax and int(np.prod([dims[q] for q in qs])) <= dmax
             in_run = all_diag and int(np.prod(dims[min(qs):max(qs) + 1])) <= (1 << 24)
-            if j < i - 1 and not (in_block or in_run):
+            in_dt = _dense_then_run(gates, dims, j, i - 1, kmax)
+            if j < i - 1 and not (in_block or in_run or in_dt):
                 break  # unions only grow as j decreases
             seg = (j, i - 1)
             if seg not in cost:
                 ts = []
-                for tc in (9, 65):
-                    L.qd_set_tuning(reg, L.QD_TUNE_TC_MIN_D, tc)
-                    ts.append(time_launch(reg, gates[j:i], reps))
-                L.qd_set_tuning(reg, L.QD_TUNE_TC_MIN_D, 0)
+                sub = L.GateArray(gates[j:i])
+                for kind, f in L.qd_segment_forms(reg, sub, 0, i - j - 1):
+                    ts.append(time_launch(reg, gates[j:i], reps, kind))
+                    if record is not None:
+                        record.append((f, ts[-1]))
                 cost[seg] = min(ts)
             c = best[j] + cost[seg]
             if c < best[i]:
@@ -314,6 +356,42 @@ def exhaustive_measured(reg: int, dims: Sequence[int], gates, kmax: int = 3, dma
         segs.append((back[i], i - 1))
         i = back[i]
     return segs[::-1], best[n]
+
+
+# Spectator sets of the training circuits (the evaluation circuits use
+# (3, 3, 3, 3, 3, 2, 2, 2, 2) and seeds from 7000).
+TRAIN_SPECTATORS = (
+    (3, 3, 3, 3, 3, 2, 2, 2, 2),
+    (2,) * 12,
+    (3,) * 8,
+    (4, 4, 4, 4, 4, 4),
+    (2, 2, 2, 2, 3, 3, 3, 3, 3, 3),
+    (3, 3, 2, 2, 2, 2, 2, 2, 2, 2, 2),
+)
+
+
+def circuit_samples(n_circuits: int, seed: int = 20000, reps: int = 3, log=None):
+    """Training samples from the planner's own queries: every candidate
+    segment of random circuits (the shape of the evaluation circuits, other
+    seeds, varied spectators), each feasible form timed.  Returns X, y."""
+    rng = np.random.default_rng(seed)
+    X, y = [], []
+    t0 = time.time()
+    for c in range(n_circuits):
+        spect = TRAIN_SPECTATORS[int(rng.integers(len(TRAIN_SPECTATORS)))]
+        dims, gates = eval_circuit(seed + c, spectators=spect)
+        h = L.qd_create(dims, None, L.QD_C64, 0, 0, 0)
+        try:
+            rec = []
+            exhaustive_measured(h, dims, gates, reps=reps, record=rec)
+            for f, ms in rec:
+                X.append(f)
+                y.append(math.log(max(ms, 1e-4) * 1e3))
+        finally:
+            L.qd_destroy(h)
+        if log and (c + 1) % 10 == 0:
+            log(f"circuits {c + 1}/{n_circuits}: {len(y)} samples, {time.time() - t0:.1f} s")
+    return np.array(X, np.float32), np.array(y, np.float32)
 
 
 def evaluate(model: int, n_circuits: int = 4, seed: int = 7000, spectators=(3, 3, 3, 3, 3, 2, 2, 2, 2),
@@ -357,6 +435,8 @@ def main(argv=None):
                     help="skip the exhaustive search over measured segment costs (slow)")
     ap.add_argument("--large-samples", type=int, default=0,
                     help="extra samples on registers above 2^31 amplitudes (64-bit index kernels)")
+    ap.add_argument("--circuit-samples", type=int, default=0,
+                    help="training circuits whose candidate segments are all timed (the planner's own queries)")
     ap.add_argument("--base-data", default=None,
                     help="npz (X, y) of earlier samples to train on together with the new ones")
     args = ap.parse_args(argv)
@@ -377,6 +457,10 @@ def main(argv=None):
         parts_y.append(y)
     if args.large_samples > 0:
         X, y = generate(args.large_samples, args.seed + 1, registers=LARGE_REGISTERS, reps=2, log=log)
+        parts_X.append(X)
+        parts_y.append(y)
+    if args.circuit_samples > 0:
+        X, y = circuit_samples(args.circuit_samples, 20000 + args.seed, log=log)
         parts_X.append(X)
         parts_y.append(y)
     X, y = np.concatenate(parts_X), np.concatenate(parts_y)

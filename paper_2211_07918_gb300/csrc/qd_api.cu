@@ -276,14 +276,18 @@ bool classify_mono(const double *M, int D, GatePlan &g) {
 // Build the launch plan of one gate: matrix M over the targets (first listed
 // most significant), controls at levels.  Returns QD_OK; sets *noop when the
 // gate is the identity.
-int plan_gate(const qd_reg *r, const double *M, const Acting &a, bool diag_only, GatePlan &g, bool *noop) {
+int plan_gate(const qd_reg *r, const double *M, const Acting &a, bool diag_only, GatePlan &g, bool *noop,
+              bool force_dense = false) {
     *noop = false;
     g = GatePlan{};
     const int D = a.D;
     g.D = D;
     g.N = (uint64_t)r->N;
     // matrix / classification
-    if (diag_only) {
+    if (force_dense) {  // the dense kernels, whatever the matrix (a dense part with a table epilogue)
+        g.kind = Kind::Dense;
+        std::memcpy(g.U, M, sizeof(double) * 2 * D * D);
+    } else if (diag_only) {
         for (int i = 0; i < D; ++i) {
             g.src[i] = i;
             g.lam[2 * i] = M[2 * i];
@@ -811,7 +815,10 @@ int qd_apply_gate(qd_reg *r, const qd_gate *gate) {
 
 namespace {
 
-RegisterShape shape_of(const qd_reg *r) { return RegisterShape{r->n, r->dims, r->s, r->N, r->prec, r->tc_min_d}; }
+RegisterShape shape_of(const qd_reg *r) {
+    const int dmax = r->fuse_dmax > 0 ? r->fuse_dmax : (r->prec == QD_C64 ? kTcMaxD : QD_MAX_D);
+    return RegisterShape{r->n, r->dims, r->s, r->N, r->prec, r->tc_min_d, dmax};
+}
 
 bool has_measure(const qd_gate *gates, int32_t ngates) {
     for (int i = 0; i < ngates; ++i)
@@ -1005,6 +1012,29 @@ int plan_diag_run(const qd_reg *r, const std::vector<FuseGate> &fg, int first, i
     return QD_OK;
 }
 
+// Launch plan of a dense part followed by a diagonal run: the dense kernel
+// (direct geometry) on the part's qudits with the run's table as epilogue;
+// the table itself is built once the plan's table buffer exists.
+int plan_dense_table(const qd_reg *r, const std::vector<FuseGate> &fg, int first, int last, int kmax, GatePlan &g,
+                     DiagRunSpec &spec) {
+    const DenseTableSplit dt = dense_table_split(fg, first, last, shape_of(r), kmax);
+    if (!dt.ok) return fail(QD_ERR_DIM, "segment is not a dense part followed by a diagonal run");
+    const FuseBlock b = build_block(fg, first, dt.split, r->dims);
+    Acting a;
+    a.k = (int)b.qudits.size();
+    a.nc = 0;
+    a.D = b.D;
+    for (int m = 0; m < a.k; ++m) a.t[m] = b.qudits[m];
+    GatePlan run;
+    if (int rc = plan_diag_run(r, fg, dt.split + 1, last, run, spec)) return rc;
+    bool noop = false;
+    if (int rc = plan_gate(r, b.M.data(), a, false, g, &noop, true)) return rc;
+    g.mode = Mode::Direct;
+    g.tab_div = run.tab_div;
+    g.tab_size = run.tab_size;
+    return QD_OK;
+}
+
 // Launch plan of one fused block: a dense gate on the block's qudits.
 int plan_block(const qd_reg *r, const FuseBlock &b, GatePlan &g) {
     Acting a;
@@ -1030,7 +1060,8 @@ namespace {
 // blocks must respect the register's QD_TUNE_FUSE_* limits (planner output
 // does by construction; explicit segmentations only need the hard limits).
 int build_plan(qd_reg *r, const std::vector<FuseGate> &fg, const std::vector<const qd_gate *> &orig,
-               const std::vector<std::pair<int, int>> &segs, const std::vector<int> &kinds, qd_plan **out) {
+               const std::vector<std::pair<int, int>> &segs, const std::vector<int> &kinds, int kmax,
+               qd_plan **out) {
     qd_plan *p = new qd_plan();
     p->reg = r;
     p->gates.reserve(segs.size());
@@ -1056,6 +1087,18 @@ int build_plan(qd_reg *r, const std::vector<FuseGate> &fg, const std::vector<con
                     if (std::find(uq.begin(), uq.end(), q) == uq.end()) uq.push_back(q);
             }
             (void)sh;
+            if (kinds[si] == kKernelDenseTable) {
+                runs.emplace_back();
+                runs.back().plan_index = (int)p->gates.size();
+                rc = plan_dense_table(r, fg, sg.first, sg.second, kmax, g, runs.back());
+                if (rc == QD_OK) {
+                    ++p->blocks;
+                    p->gates.push_back(g);
+                    continue;
+                }
+                delete p;
+                return rc;
+            }
             if (kinds[si] == kKernelDiagTable) {
                 runs.emplace_back();
                 runs.back().plan_index = (int)p->gates.size();
@@ -1163,13 +1206,33 @@ int qd_plan_create(qd_reg *r, const qd_gate *gates, int32_t ngates, int32_t plan
     std::vector<std::pair<int, int>> segs;
     std::vector<int> kinds;
     if ((rc = segments_for(r, fg, plan_kind, segs, kinds, nullptr))) return rc;
-    rc = build_plan(r, fg, orig, segs, kinds, out);
+    rc = build_plan(r, fg, orig, segs, kinds, r->fuse_kmax, out);
     if (rc == QD_OK) (*out)->measure_after = has_measure(gates, ngates);
     return rc;
 }
 
+static_assert(kKernelMono == QD_FORM_MONO && kKernelDense == QD_FORM_DENSE && kKernelBlock == QD_FORM_BLOCK &&
+                  kKernelBlockTc == QD_FORM_BLOCK_TC && kKernelDiagTable == QD_FORM_DIAG_RUN &&
+                  kKernelDenseTable == QD_FORM_DENSE_RUN,
+              "kernel forms of the planner and the C ABI differ");
+
+namespace {
+// The register's shape with the hard block limits of an explicit
+// segmentation (not the register's fusion limits).
+RegisterShape hard_shape(const qd_reg *r) {
+    RegisterShape sh = shape_of(r);
+    sh.fuse_dmax = r->prec == QD_C64 ? kTcMaxD : QD_MAX_D;
+    return sh;
+}
+}  // namespace
+
 int qd_plan_create_segmented(qd_reg *r, const qd_gate *gates, int32_t ngates, const int32_t *seg_first,
                              const int32_t *seg_last, int32_t nseg, qd_plan **out) {
+    return qd_plan_create_forms(r, gates, ngates, seg_first, seg_last, nullptr, nseg, out);
+}
+
+int qd_plan_create_forms(qd_reg *r, const qd_gate *gates, int32_t ngates, const int32_t *seg_first,
+                         const int32_t *seg_last, const int32_t *seg_kind, int32_t nseg, qd_plan **out) {
     if (!out) return fail(QD_ERR_ARG, "null output handle");
     *out = nullptr;
     if (int rc = reg_ok(r)) return rc;
@@ -1192,24 +1255,42 @@ int qd_plan_create_segmented(qd_reg *r, const qd_gate *gates, int32_t ngates, co
         if (sg.first == sg.second) continue;
         std::vector<int> qs;
         int64_t D = 1;
-        for (int gi = sg.first; gi <= sg.second; ++gi)
+        bool all_diag = true;
+        for (int gi = sg.first; gi <= sg.second; ++gi) {
+            all_diag = all_diag && fg[gi].diag;
             for (int q : fg[gi].acting)
                 if (std::find(qs.begin(), qs.end(), q) == qs.end()) {
                     qs.push_back(q);
-                    D *= r->dims[q];
+                    D = std::min<int64_t>(D * r->dims[q], int64_t(1) << 40);
                 }
+        }
+        // a run of diagonal gates may span any qudits whose range table fits,
+        // and so may a dense part of at most 16 states followed by such a run
+        if (all_diag && diag_table_size(shape_of(r), qs) <= kDiagRunMaxTable) continue;
+        if (dense_table_split(fg, sg.first, sg.second, shape_of(r), QD_MAX_TARGETS).ok) continue;
         const int64_t cap = r->prec == QD_C64 ? kTcMaxD : QD_MAX_D;
         if ((int)qs.size() > QD_MAX_TARGETS || D > cap) return fail(QD_ERR_DIM, "segment block too large");
     }
-    // kernels of the given segments as the register's cost model prices them
+    // kernels of the given segments as the register's cost model prices them,
+    // within the hard block limits rather than the register's fusion limits
+    // (or as given: each given form must be one of the segment's feasible ones)
     std::vector<int> kinds(segs.size(), 0);
     {
-        const RegisterShape sh = shape_of(r);
+        const RegisterShape sh = hard_shape(r);
         const CostFn cost = cost_for(r, QD_PLAN_GREEDY);
-        for (size_t i = 0; i < segs.size(); ++i)
-            segment_cost(fg, segs[i].first, segs[i].second, sh, cost, r->fuse_kmax, &kinds[i]);
+        for (size_t i = 0; i < segs.size(); ++i) {
+            if (!seg_kind || seg_kind[i] < 0) {
+                segment_cost(fg, segs[i].first, segs[i].second, sh, cost, QD_MAX_TARGETS, &kinds[i]);
+                continue;
+            }
+            bool ok = false;
+            for (const LaunchFeatures &f : segment_forms(fg, segs[i].first, segs[i].second, sh, QD_MAX_TARGETS))
+                ok = ok || (int)f.f[10] == seg_kind[i];
+            if (!ok) return fail(QD_ERR_ARG, "kernel form not feasible for the segment");
+            kinds[i] = seg_kind[i];
+        }
     }
-    rc = build_plan(r, fg, orig, segs, kinds, out);
+    rc = build_plan(r, fg, orig, segs, kinds, QD_MAX_TARGETS, out);
     if (rc == QD_OK) (*out)->measure_after = has_measure(gates, ngates);
     return rc;
 }
@@ -1227,13 +1308,33 @@ int qd_segment_features(qd_reg *r, const qd_gate *gates, int32_t ngates, int32_t
     std::vector<const qd_gate *> orig;
     if (int rc = collect_gates(r, gates, ngates, fg, orig)) return rc;
     if (first < 0 || last < first || last >= (int)fg.size()) return fail(QD_ERR_ARG, "bad segment");
-    const RegisterShape sh = shape_of(r);
-    CostFn grab = [out](const LaunchFeatures &f) {
-        std::copy(f.f, f.f + kFeatures, out);
-        return 0.0;
-    };
-    segment_cost(fg, first, last, sh, grab, r->fuse_kmax);
-    return QD_OK;
+    // the form an explicit segmentation of this segment runs
+    const RegisterShape sh = hard_shape(r);
+    int kind = -1;
+    segment_cost(fg, first, last, sh, cost_for(r, QD_PLAN_GREEDY), QD_MAX_TARGETS, &kind);
+    for (const LaunchFeatures &f : segment_forms(fg, first, last, sh, QD_MAX_TARGETS))
+        if ((int)f.f[10] == kind) {
+            std::copy(f.f, f.f + kFeatures, out);
+            return QD_OK;
+        }
+    return fail(QD_ERR_ARG, "segment has no feasible form");
+}
+
+int qd_segment_forms(qd_reg *r, const qd_gate *gates, int32_t ngates, int32_t first, int32_t last, int32_t *kinds,
+                     float *features, int32_t cap, int32_t *nforms) {
+    if (int rc = reg_ok(r)) return rc;
+    if (!nforms || cap < 0 || (cap > 0 && (!kinds || !features))) return fail(QD_ERR_ARG, "bad output arrays");
+    std::vector<FuseGate> fg;
+    std::vector<const qd_gate *> orig;
+    if (int rc = collect_gates(r, gates, ngates, fg, orig)) return rc;
+    if (first < 0 || last < first || last >= (int)fg.size()) return fail(QD_ERR_ARG, "bad segment");
+    const std::vector<LaunchFeatures> forms = segment_forms(fg, first, last, hard_shape(r), QD_MAX_TARGETS);
+    *nforms = (int32_t)forms.size();
+    for (int i = 0; i < (int)forms.size() && i < cap; ++i) {
+        kinds[i] = (int32_t)forms[i].f[10];
+        std::copy(forms[i].f, forms[i].f + kFeatures, features + (size_t)i * kFeatures);
+    }
+    return (int)forms.size() > cap ? fail(QD_ERR_OOM, "more forms than the arrays hold") : QD_OK;
 }
 
 namespace {
@@ -1339,6 +1440,7 @@ int qd_plan_timings(qd_plan *p, float *ms, double *alg_bytes, int32_t *kclass) {
                                           : (g.mode == Mode::Direct ? QD_KCLASS_MONO_DIRECT : QD_KCLASS_MONO_TILE);
             if (g.mode == Mode::Tensor) c = QD_KCLASS_TENSOR_BLOCK;
             if (g.mode == Mode::Table) c = QD_KCLASS_DIAG_TABLE;
+            if (g.mode == Mode::Direct && g.tab) c = QD_KCLASS_DENSE_TABLE;
             kclass[i] = c | (g.D << 8);
         }
     }

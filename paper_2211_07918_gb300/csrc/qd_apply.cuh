@@ -172,7 +172,7 @@ __host__ __device__ constexpr int direct_unroll() {
 }
 template <typename T, typename I, int MD>
 __host__ __device__ constexpr int mono_unroll() {
-    return MD <= 4 ? 2 : 1;
+    return MD <= 2 ? 4 : (MD <= 4 ? 2 : 1);
 }
 // Resident CTAs of 256 threads the register budget must allow (the memory
 // parallelism of these kernels is the loads all their threads have in
@@ -282,6 +282,132 @@ __global__ void __launch_bounds__(256, (direct_min_blocks<T, MD, false>())) k_mo
                 if (ok[u] && ((a.active >> i) & 1u))
                     a.psi[base[u] + a.off[i]] =
                         ((a.unit >> i) & 1u) ? w[u][i] : cmul_split<T>(a.lam[i], a.lamlo[kSplit<T> ? i : 0], w[u][i]);
+    }
+}
+
+// Dense gate followed by a run of diagonal gates, one pass: out = U v for
+// every group, then each output amplitude at flat index i is multiplied by
+// the run's table entry T[(i / s_qa) mod TS] (the product of the run's
+// diagonals; complex64 entries as FP32 hi + lo, applied lo first).
+template <typename I> struct DivOfI;
+template <> struct DivOfI<uint32_t> { using type = FastDiv32; };
+template <> struct DivOfI<uint64_t> { using type = FastDiv64; };
+
+template <typename T> struct TabEntry;
+template <> struct TabEntry<float> { using type = float4; };
+template <> struct TabEntry<double> { using type = double2; };
+
+template <typename T, typename I, int MD>
+struct DenseTableArgs {
+    DenseDirectArgs<T, I, MD> d;
+    typename DivOfI<I>::type divA, divT;  // by s_qa and by TS
+    uint32_t oq[MD];  // (off_j / s_qa) mod TS
+    I orm[MD];        // off_j mod s_qa
+    const typename TabEntry<T>::type *tab;
+};
+
+template <typename T>
+__device__ __forceinline__ v2<T> times_entry(const v2<T> o, const typename TabEntry<T>::type t) {
+    if constexpr (kSplit<T>) {
+        return cmul_split<T>(mk<T>(t.x, t.y), mk<T>(t.z, t.w), o);
+    } else {
+        return cmul<T>(mk<T>(t.x, t.y), o);
+    }
+}
+
+// Two groups per thread per iteration for up to four members.  The table
+// index of member j of a group at base b is, with b = qb s_qa + rb,
+// (qb + off_j / s_qa + [rb + off_j mod s_qa >= s_qa]) mod TS (< 2^24): two
+// divisions per group instead of two per member.  The table entries of a
+// group's outputs are loaded before the first of them is stored (a load
+// after a store to the state could not be moved above it, and each output
+// would wait out its own table latency): all of them for up to four
+// members, pairs above (register budget).  The kernel is bound by the loads
+// its resident threads keep in flight, so complex64 keeps 4 CTAs of 256
+// threads per SM (64 registers; a group's table position is computed after
+// its member loads are issued, which keeps it within them).
+template <typename T, typename I, int MD>
+__host__ __device__ constexpr int table_min_blocks() {
+    return kSplit<T> ? 4 : direct_min_blocks<T, MD, true>();
+}
+
+template <typename T, typename I, int MD, bool EX>
+__global__ void __launch_bounds__(256, (table_min_blocks<T, I, MD>()))
+    k_dense_table(const __grid_constant__ DenseTableArgs<T, I, MD> a) {
+    constexpr int UN = MD <= 4 ? 2 : 1;
+    constexpr int TB = MD <= 4 ? MD : 2;  // outputs whose entries are loaded together
+    using Entry = typename TabEntry<T>::type;
+    const int D = EX ? MD : a.d.D;
+    const I step = (I)gridDim.x * blockDim.x;
+    const I sA = (I)a.divA.d;
+    const uint32_t TS = (uint32_t)a.divT.d;
+    for (I r0 = (I)blockIdx.x * blockDim.x + threadIdx.x; r0 < a.d.R; r0 += UN * step) {
+        I base[UN];
+        bool ok[UN];
+        v2<T> v[UN][MD];
+#pragma unroll
+        for (int u = 0; u < UN; ++u) {
+            const I r = r0 + u * step;
+            ok[u] = r < a.d.R;
+            base[u] = ok[u] ? expand(r, a.d.ex) + a.d.base : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < UN; ++u)
+#pragma unroll
+            for (int j = 0; j < MD; ++j)
+                v[u][j] = (ok[u] && (EX || j < D)) ? a.d.psi[base[u] + a.d.off[j]] : mk<T>(T(0), T(0));
+#pragma unroll
+        for (int u = 0; u < UN; ++u) {
+            if (!ok[u]) continue;
+            // the group's table position (while its member loads are in flight)
+            const I qb = fdiv(base[u], a.divA);
+            const I rb = base[u] - qb * sA;
+            const uint32_t kb = (uint32_t)(qb - fdiv(qb, a.divT) * (I)TS);
+#pragma unroll
+            for (int c0 = 0; c0 < MD; c0 += TB) {
+                Entry t[TB];
+#pragma unroll
+                for (int c = 0; c < TB; ++c) {
+                    const int i = c0 + c;
+                    if (EX || i < D) {
+                        uint32_t k = kb + a.oq[i] + (rb + a.orm[i] >= sA ? 1u : 0u);
+                        if (k >= TS) k -= TS;
+                        if (k >= TS) k -= TS;
+                        t[c] = __ldg(&a.tab[k]);
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < TB; ++c) {
+                    const int i = c0 + c;
+                    if (!(EX || i < D)) continue;
+                    v2<T> acc = mk<T>(T(0), T(0));
+                    if constexpr (kPacked<T, MD>) {
+                        // lo terms first, then hi terms, two lanes per FMA
+                        f2p pa = 0ull;
+#pragma unroll
+                        for (int j = 0; j < MD; ++j) {
+                            pa = pk_fma(a.d.Pk[4 * (i * MD + j) + 0], pk_pack(v[u][j].x, v[u][j].y), pa);
+                            pa = pk_fma(a.d.Pk[4 * (i * MD + j) + 1], pk_pack(v[u][j].y, v[u][j].x), pa);
+                        }
+#pragma unroll
+                        for (int j = 0; j < MD; ++j) {
+                            pa = pk_fma(a.d.Pk[4 * (i * MD + j) + 2], pk_pack(v[u][j].x, v[u][j].y), pa);
+                            pa = pk_fma(a.d.Pk[4 * (i * MD + j) + 3], pk_pack(v[u][j].y, v[u][j].x), pa);
+                        }
+                        const float2 o = pk_unpack(pa);
+                        acc = mk<T>(o.x, o.y);
+                    } else {
+                        if constexpr (kSplit<T>) {
+#pragma unroll
+                            for (int j = 0; j < MD; ++j) cmac<T>(acc, a.d.Ulo[i * MD + j], v[u][j]);
+                        }
+#pragma unroll
+                        for (int j = 0; j < MD; ++j) cmac<T>(acc, a.d.U[i * MD + j], v[u][j]);
+                    }
+                    a.d.psi[base[u] + a.d.off[i]] = times_entry<T>(acc, t[c]);
+                }
+            }
+        }
     }
 }
 
@@ -453,6 +579,24 @@ inline void fill_matrix(v2<T> *U, v2<T> *Ulo, const GatePlan &g) {
     if constexpr (!kSplit<T>) Ulo[0] = mk<T>(T(0), T(0));
 }
 
+// Packed coefficient pairs of a dense matrix (complex64, MD <= 4), from the
+// hi / lo entries fill_matrix wrote.
+template <typename T, typename I, int MD>
+inline void fill_packed(DenseDirectArgs<T, I, MD> &a) {
+    if constexpr (kPacked<T, MD>) {
+        for (int k = 0; k < MD * MD; ++k) {
+            const float hx = (float)a.U[k].x, hy = (float)a.U[k].y;
+            const float lx = (float)a.Ulo[k].x, ly = (float)a.Ulo[k].y;
+            a.Pk[4 * k + 0] = pk_host(lx, lx);
+            a.Pk[4 * k + 1] = pk_host(-ly, ly);
+            a.Pk[4 * k + 2] = pk_host(hx, hx);
+            a.Pk[4 * k + 3] = pk_host(-hy, hy);
+        }
+    } else {
+        a.Pk[0] = 0;
+    }
+}
+
 template <typename T, int MD>
 inline void fill_lam(v2<T> *lam, v2<T> *lamlo, const GatePlan &g) {
     for (int i = 0; i < MD; ++i) {
@@ -489,18 +633,7 @@ cudaError_t launch_dense(const GatePlan &g, void *psi, int sm_count, cudaStream_
         a.ex = expand_for<I>(g.ex);
         for (int j = 0; j < MD; ++j) a.off[j] = j < g.D ? (I)g.off[j] : 0;
         fill_matrix<T, MD>(a.U, a.Ulo, g);
-        if constexpr (kPacked<T, MD>) {
-            for (int k = 0; k < MD * MD; ++k) {
-                const float hx = (float)a.U[k].x, hy = (float)a.U[k].y;
-                const float lx = (float)a.Ulo[k].x, ly = (float)a.Ulo[k].y;
-                a.Pk[4 * k + 0] = pk_host(lx, lx);
-                a.Pk[4 * k + 1] = pk_host(-ly, ly);
-                a.Pk[4 * k + 2] = pk_host(hx, hx);
-                a.Pk[4 * k + 3] = pk_host(-hy, hy);
-            }
-        } else {
-            a.Pk[0] = 0;
-        }
+        fill_packed<T, I, MD>(a);
         auto fn = k_dense_direct<T, I, MD, EX>;
         const int grid = grid_of(g.R, kBlock, sm_count, occupancy_blocks((const void *)fn, kBlock, 0));
         if (grid <= 0) return cudaSuccess;
@@ -570,9 +703,51 @@ cudaError_t launch_mono(const GatePlan &g, void *psi, int sm_count, cudaStream_t
     return cudaGetLastError();
 }
 
+template <typename T, typename I, int MD, bool EX>
+cudaError_t launch_dense_table(const GatePlan &g, void *psi, int sm_count, cudaStream_t s) {
+    DenseTableArgs<T, I, MD> a;
+    a.d.psi = static_cast<v2<T> *>(psi);
+    a.d.R = (I)g.R;
+    a.d.base = (I)g.base_off;
+    a.d.D = g.D;
+    a.d.ex = expand_for<I>(g.ex);
+    for (int j = 0; j < MD; ++j) a.d.off[j] = j < g.D ? (I)g.off[j] : 0;
+    fill_matrix<T, MD>(a.d.U, a.d.Ulo, g);
+    fill_packed<T, I, MD>(a.d);
+    if constexpr (sizeof(I) == 4) {
+        a.divA = make_fastdiv32((uint32_t)g.tab_div);
+        a.divT = make_fastdiv32((uint32_t)g.tab_size);
+    } else {
+        a.divA = make_fastdiv64(g.tab_div);
+        a.divT = make_fastdiv64(g.tab_size);
+    }
+    for (int j = 0; j < MD; ++j) {
+        const uint64_t o = j < g.D ? (uint64_t)g.off[j] : 0;
+        a.oq[j] = (uint32_t)((o / g.tab_div) % g.tab_size);
+        a.orm[j] = (I)(o % g.tab_div);
+    }
+    a.tab = static_cast<const typename TabEntry<T>::type *>(g.tab);
+    auto fn = k_dense_table<T, I, MD, EX>;
+    const int grid = grid_of(g.R, kBlock, sm_count, occupancy_blocks((const void *)fn, kBlock, 0));
+    if (grid <= 0) return cudaSuccess;
+    fn<<<grid, kBlock, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 template <typename T, typename I>
 cudaError_t launch_gate_ti(const GatePlan &g, void *psi, int sm_count, cudaStream_t s) {
+    if (g.tab) {  // dense part + diagonal-run table (D <= 16, direct geometry)
+        switch (g.D) {
+            case 2: return launch_dense_table<T, I, 2, true>(g, psi, sm_count, s);
+            case 3: return launch_dense_table<T, I, 3, true>(g, psi, sm_count, s);
+            case 4: return launch_dense_table<T, I, 4, true>(g, psi, sm_count, s);
+            default: break;
+        }
+        if (g.D <= 8) return launch_dense_table<T, I, 8, false>(g, psi, sm_count, s);
+        return launch_dense_table<T, I, 16, false>(g, psi, sm_count, s);
+    }
     if (g.kind == Kind::Mono) {
+        if (g.D <= 2) return launch_mono<T, I, 2>(g, psi, sm_count, s);
         if (g.D <= 4) return launch_mono<T, I, 4>(g, psi, sm_count, s);
         if (g.D <= 8) return launch_mono<T, I, 8>(g, psi, sm_count, s);
         if (g.D <= 16) return launch_mono<T, I, 16>(g, psi, sm_count, s);

@@ -189,18 +189,37 @@ uint64_t diag_table_size(const RegisterShape &reg, const std::vector<int> &qudit
     return T;
 }
 
+DenseTableSplit dense_table_split(const std::vector<FuseGate> &gates, int first, int last, const RegisterShape &reg,
+                                  int kmax) {
+    DenseTableSplit d;
+    int k = last;
+    while (k >= first && gates[k].diag) --k;
+    d.split = k;
+    if (k < first || k == last) return d;  // all diagonal, or no diagonal suffix
+    d.dense_q = union_qudits(gates, first, k);
+    d.run_q = union_qudits(gates, k + 1, last);
+    d.dense_D = dim_of(d.dense_q, reg.dims);
+    d.table = diag_table_size(reg, d.run_q);
+    d.ok = (int)d.dense_q.size() <= kmax && d.dense_D <= kDenseTableMaxD && d.table <= kDiagRunMaxTable;
+    return d;
+}
+
 double analytic_cost(const RegisterShape &reg, const LaunchFeatures &lf) {
     const double D = std::exp2((double)lf.f[0]);
     const bool c128 = lf.f[9] > 0.5f;
     const bool dense = lf.f[10] > 0.5f;
     const bool block = lf.f[10] > 2.5f && lf.f[10] < 3.5f;  // fused block on the tensor cores
-    const bool table = lf.f[10] > 3.5f;                    // diagonal run through a table
-    const double touched = (double)reg.N * std::exp2((double)lf.f[11]);
+    const bool table = lf.f[10] > 3.5f && lf.f[10] < 4.5f; // diagonal run through a table
+    const bool dense_table = lf.f[10] > 4.5f;              // dense part + diagonal table
+    // feature 11: log2 of the control-slice fraction, or (dense + table) of the table entries
+    const double touched = dense_table ? (double)reg.N : (double)reg.N * std::exp2((double)lf.f[11]);
     const double b = c128 ? 16.0 : 8.0;
     double t_mem = 2.0 * touched * b / 5.0e12;
     if (table) t_mem += std::exp2((double)lf.f[0]) * 16.0 / 5.0e12;
+    if (dense_table) t_mem += std::exp2((double)lf.f[11]) * 16.0 / 5.0e12;
     double t_cmp = table ? touched * 40.0 / 2.0e13 : 0.0;  // index arithmetic per amplitude
-    if (dense && !table) {
+    if (dense_table) t_cmp = c128 ? touched * 4.0 * D / 0.5e12 : touched * (8.0 * D + 64.0) / 2.0e13;
+    if (dense && !table && !dense_table) {
         if (!c128 && block) {
             // fused block on the tensor cores: 6 exact BF16 slice products of
             // (2 Dp) x (2 Dp) per group; measured on GB300 the kernel moves
@@ -238,20 +257,45 @@ double segment_cost(const std::vector<FuseGate> &gates, int first, int last, con
         all_mono = all_mono && gates[i].mono;
         all_diag = all_diag && gates[i].diag;
     }
+    // the segment's feasible forms: a block (or a diagonal run), and a dense
+    // part followed by a diagonal run
     int kinds[2];
-    const int nk = block_kernels(reg, D, (int)s.size(), kmax, all_mono, all_diag, kinds);
-    double best = 0.0;
+    int nk = 0;
+    if (((int)s.size() <= kmax && D <= reg.fuse_dmax) ||
+        (all_diag && diag_table_size(reg, s) <= kDiagRunMaxTable))
+        nk = block_kernels(reg, D, (int)s.size(), kmax, all_mono, all_diag, kinds);
+    double best = std::numeric_limits<double>::infinity();
     for (int k = 0; k < nk; ++k) {
         const int kind = kinds[k];
         const double c = kind == kKernelDiagTable
                              ? cost(launch_features(reg, s, (int)diag_table_size(reg, s), kind, 1.0))
                              : cost(launch_features(reg, s, (int)D, kind, 1.0));
-        if (k == 0 || c < best) {
+        if (c < best) {
             best = c;
             if (kind_out) *kind_out = kind;
         }
     }
+    const DenseTableSplit dt = dense_table_split(gates, first, last, reg, kmax);
+    if (dt.ok) {
+        const double c =
+            cost(launch_features(reg, dt.dense_q, (int)dt.dense_D, kKernelDenseTable, (double)dt.table));
+        if (c < best) {
+            best = c;
+            if (kind_out) *kind_out = kKernelDenseTable;
+        }
+    }
     return best;
+}
+
+std::vector<LaunchFeatures> segment_forms(const std::vector<FuseGate> &gates, int first, int last,
+                                          const RegisterShape &reg, int kmax) {
+    std::vector<LaunchFeatures> out;
+    const CostFn grab = [&out](const LaunchFeatures &f) {
+        out.push_back(f);
+        return 0.0;
+    };
+    segment_cost(gates, first, last, reg, grab, kmax);
+    return out;
 }
 
 namespace {
@@ -265,7 +309,8 @@ bool feasible(const std::vector<FuseGate> &gates, int first, int last, const Reg
     bool all_diag = true;
     for (int i = first; i <= last && all_diag; ++i) all_diag = gates[i].diag;
     if (all_diag && diag_table_size(reg, s) <= kDiagRunMaxTable) return true;
-    return (int)s.size() <= kmax && dim_of(s, reg.dims) <= Dmax;
+    if ((int)s.size() <= kmax && dim_of(s, reg.dims) <= Dmax) return true;
+    return dense_table_split(gates, first, last, reg, kmax).ok;
 }
 }  // namespace
 

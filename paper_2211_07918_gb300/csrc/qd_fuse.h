@@ -47,6 +47,7 @@ struct RegisterShape {
     int precision;  // 1 = complex64, 2 = complex128
     int tc_min_d;   // complex64 fused blocks with D >= tc_min_d (or D > 32) run on the tensor cores;
                     // 0: the cost model chooses per block between the CUDA cores and the tensor cores
+    int fuse_dmax;  // largest dimension of a fused block
 };
 
 // Kernel kind of a launch (feature 10).
@@ -55,6 +56,8 @@ constexpr int kKernelDense = 1;  // per-gate dense (CUDA cores)
 constexpr int kKernelBlock = 2;    // fused block on the CUDA-core dense kernels (D <= 32)
 constexpr int kKernelBlockTc = 3;  // fused block on the tensor cores (complex64)
 constexpr int kKernelDiagTable = 4;  // run of diagonal gates applied through one table (any qudit count)
+constexpr int kKernelDenseTable = 5; // dense gate or block followed by a diagonal run, one launch
+constexpr int kDenseTableMaxD = 16;  // largest dense part of such a launch
 constexpr uint64_t kDiagRunMaxTable = uint64_t(1) << 24;  // entries of a diagonal run's table
 constexpr int kMonoBlockMaxD = 32;  // a fused block of permutations with phases up to this D runs as mono
 constexpr int kDenseBlockMaxD = 32;  // largest fused block the CUDA-core dense kernels take
@@ -73,6 +76,22 @@ int block_kernels(const RegisterShape &reg, int64_t D, int nq, int kmax, bool al
 // Entries of the table of a diagonal run over `qudits`: the product of the
 // dimensions of the contiguous range [min, max] of those qudits.
 uint64_t diag_table_size(const RegisterShape &reg, const std::vector<int> &qudits);
+
+// A multi-gate segment as a dense part followed by a diagonal run: split is
+// the last gate of the dense part (the segment's maximal all-diagonal suffix
+// starts after it; -1 when the whole segment is diagonal); ok when the dense
+// part spans at most kmax qudits and kDenseTableMaxD states and the run's
+// table fits kDiagRunMaxTable.  dense_q: the dense part's qudits; run_q: the
+// run's; table: the run's table entries.
+struct DenseTableSplit {
+    bool ok = false;
+    int split = -1;
+    std::vector<int> dense_q, run_q;
+    int64_t dense_D = 1;
+    uint64_t table = 0;
+};
+DenseTableSplit dense_table_split(const std::vector<FuseGate> &gates, int first, int last, const RegisterShape &reg,
+                                  int kmax);
 
 // Feature vector of a launch acting on `qudits` with target dimension D:
 // log2 D, qudit count, log2 of the (up to three) smallest strides, relative
@@ -105,5 +124,10 @@ std::vector<std::pair<int, int>> segment_exhaustive(const std::vector<FuseGate> 
 // is the block limit that decides between a mono block and a diagonal table.
 double segment_cost(const std::vector<FuseGate> &gates, int first, int last, const RegisterShape &reg,
                     const CostFn &cost, int kmax, int *kind = nullptr);
+
+// Launch features of every feasible form of one segment (the candidates
+// segment_cost weighs; the kernel class is feature 10).
+std::vector<LaunchFeatures> segment_forms(const std::vector<FuseGate> &gates, int first, int last,
+                                          const RegisterShape &reg, int kmax);
 
 }  // namespace qd

@@ -324,6 +324,18 @@ __global__ void __launch_bounds__(TcCfg<MAXD>::THREADS, 1) k_block_tc(const __gr
 #pragma unroll
             for (int j = 0; j < C::RA; ++j)
                 v[j] = (valid && j0 + j < a.D) ? a.psi[base + a.off[j0 + j]] : make_float2(0.f, 0.f);
+            if constexpr (!C::PRE) {
+                // above D = 32 one producer group serves every tile, so its loads
+                // wait out the full memory latency: the same amplitudes of its
+                // next tile go into L2 now and the next loads wait for L2 only
+                const I gn = g + (I)NGRP * (I)gridDim.x * (I)kTcRows;
+                if (i + NGRP < nlocal && gn < a.R) {
+                    const I bn = expand(gn, a.ex);
+#pragma unroll
+                    for (int j = 0; j < C::RA; ++j)
+                        if (j0 + j < a.D) asm volatile("prefetch.global.L2 [%0];" ::"l"(a.psi + bn + a.off[j0 + j]));
+                }
+            }
             float amax = 0.f;
 #pragma unroll
             for (int j = 0; j < C::RA; ++j) amax = fmaxf(amax, fmaxf(fabsf(v[j].x), fabsf(v[j].y)));

@@ -24,6 +24,8 @@ QD_OUT_AMPLITUDE, QD_OUT_PROBABILITY = 0, 1
 QD_PLAN_NONE, QD_PLAN_GREEDY, QD_PLAN_LEARNED, QD_PLAN_EXHAUSTIVE = 0, 1, 2, 3
 QD_MAX_TARGETS, QD_MAX_CONTROLS = 6, 8
 QD_TUNE_TILE_STRIDE, QD_TUNE_FUSE_KMAX, QD_TUNE_FUSE_DMAX, QD_TUNE_TC_MIN_D = 1, 2, 3, 4
+# kernel forms of one launch (launch feature 10)
+QD_FORM_MONO, QD_FORM_DENSE, QD_FORM_BLOCK, QD_FORM_BLOCK_TC, QD_FORM_DIAG_RUN, QD_FORM_DENSE_RUN = range(6)
 QD_MODEL_FEATURES, QD_MODEL_PARAMS = 12, 9217
 QD_BATCH_TILE_AMPS, QD_BATCH_CTAS_PER_SM, QD_BATCH_SMALL_AMPS, QD_BATCH_GROUP_AMPS = 1, 2, 3, 4
 QD_BATCH_TILES_PER_ITEM, QD_BATCH_POLL_LIMIT = 5, 6
@@ -101,6 +103,8 @@ _SIGS = {
     "qd_set_cost_model": [_vp, _vp],
     "qd_segment_features": [_vp, ctypes.POINTER(QdGate), _i32, _i32, _i32, ctypes.POINTER(ctypes.c_float)],
     "qd_plan_create_segmented": [_vp, ctypes.POINTER(QdGate), _i32, _i32p, _i32p, _i32, ctypes.POINTER(_vp)],
+    "qd_plan_create_forms": [_vp, ctypes.POINTER(QdGate), _i32, _i32p, _i32p, _i32p, _i32, ctypes.POINTER(_vp)],
+    "qd_segment_forms": [_vp, ctypes.POINTER(QdGate), _i32, _i32, _i32, _i32p, ctypes.POINTER(ctypes.c_float), _i32, _i32p],
     "qd_batch_create": [_i32, _i32p, _i32p, _vp, ctypes.POINTER(_vp)],
     "qd_batch_set_circuit": [_vp, _i32, ctypes.POINTER(QdGate), _i32],
     "qd_batch_tune": [_vp, _i32, _i64],
@@ -308,7 +312,7 @@ def qd_plan_profile(plan: int, enable: bool = True) -> None:
 
 
 KCLASS_NAMES = {0: "dense_direct", 1: "dense_tile", 2: "mono_direct", 3: "mono_tile", 4: "tensor_block",
-                5: "diag_table"}
+                5: "diag_table", 6: "dense_table"}
 
 
 def qd_plan_timings(plan: int, with_times: bool = True):
@@ -657,13 +661,35 @@ def qd_segment_features(reg: int, gates, first: int, last: int) -> np.ndarray:
     return out
 
 
-def qd_plan_create_segmented(reg: int, gates, segments) -> int:
+def qd_plan_create_segmented(reg: int, gates, segments, kinds=None) -> int:
+    """Plan from explicit (first, last) segments; kinds: the kernel class of
+    each segment (-1: the cost model's choice), None: all chosen."""
     ga = gates if isinstance(gates, GateArray) else GateArray(gates)
     f, fp = _arr_i32([a for a, _ in segments])
     l, lp = _arr_i32([b for _, b in segments])
     out = _vp()
-    _check(load().qd_plan_create_segmented(_vp(reg), ga.ptr, ga.n, fp, lp, len(segments), ctypes.byref(out)))
+    if kinds is None:
+        _check(load().qd_plan_create_segmented(_vp(reg), ga.ptr, ga.n, fp, lp, len(segments), ctypes.byref(out)))
+    else:
+        k, kp = _arr_i32([int(x) for x in kinds])
+        _check(load().qd_plan_create_forms(_vp(reg), ga.ptr, ga.n, fp, lp, kp, len(segments), ctypes.byref(out)))
     return out.value
+
+
+def qd_plan_create_forms(reg: int, gates, segments, kinds) -> int:
+    """Plan from explicit segments with the kernel form of each given."""
+    return qd_plan_create_segmented(reg, gates, segments, list(kinds))
+
+
+def qd_segment_forms(reg: int, gates, first: int, last: int):
+    """[(kernel class, 12 features)] of every feasible form of one segment."""
+    ga = gates if isinstance(gates, GateArray) else GateArray(gates)
+    k, kp = _arr_i32([0] * 4)
+    feats = np.zeros((4, QD_MODEL_FEATURES), np.float32)
+    n = _i32(0)
+    _check(load().qd_segment_forms(_vp(reg), ga.ptr, ga.n, first, last, kp, feats.ctypes.data_as(_fp), 4,
+                                   ctypes.byref(n)))
+    return [(int(k[i]), feats[i].copy()) for i in range(n.value)]
 
 
 # ---- batched persistent execution -----------------------------------------

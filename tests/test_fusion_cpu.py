@@ -55,13 +55,40 @@ def test_block_equals_sequential_gates(seed):
         assert np.max(np.abs(M @ M.conj().T - np.eye(M.shape[0]))) <= 1e-12
 
 
+def _is_diag(g):
+    return g.kind in ("Z", "DIAG")
+
+
+def _range_table(dims, qs):
+    return int(np.prod(dims[min(qs):max(qs) + 1]))
+
+
 def _feasible(gates, dims, a, b, kmax, dmax):
+    """The planner's segment forms, restated: a block within the limits; a run
+    of diagonal gates whose covering qudit range has at most 2^24 states; a
+    dense part (<= kmax qudits, <= 16 states) followed by such a run."""
     if a == b:
         return True
     s = set()
     for g in gates[a:b + 1]:
         s |= set(_acting(g, dims))
-    return len(s) <= kmax and int(np.prod([dims[q] for q in s])) <= dmax
+    if len(s) <= kmax and int(np.prod([dims[q] for q in s])) <= dmax:
+        return True
+    if all(_is_diag(g) for g in gates[a:b + 1]):
+        return _range_table(dims, s) <= 1 << 24
+    k = b
+    while k >= a and _is_diag(gates[k]):
+        k -= 1
+    if k == b:
+        return False
+    pre = set()
+    for g in gates[a:k + 1]:
+        pre |= set(_acting(g, dims))
+    run = set()
+    for g in gates[k + 1:b + 1]:
+        run |= set(_acting(g, dims))
+    return (len(pre) <= kmax and int(np.prod([dims[q] for q in pre])) <= 16
+            and _range_table(dims, run) <= 1 << 24)
 
 
 @pytest.mark.parametrize("prec", [L.QD_C64, L.QD_C128])
@@ -71,7 +98,8 @@ def test_exhaustive_equals_brute_force(seed, prec):
     dims = [int(x) for x in rng.choice([2, 3, 4], size=5)] + [3] * 9
     n = int(rng.integers(6, 13))
     gates = _circuit(rng, dims, n)
-    kmax, dmax = 3, 32
+    # the register's default fusion limits, which qd_debug_segment_cost prices with
+    kmax, dmax = 3, (64 if prec == L.QD_C64 else 32)
     cost = {}
     for a in range(n):
         for b in range(a, n):
@@ -135,17 +163,24 @@ def test_segment_of_permutations_is_costed_as_mono():
 def test_diagonal_runs_are_planned_as_single_segments():
     """In the d-ary QFT the controlled phases onto one target (Sec. 2.1.2 phase
     gates, controlled) form a run of diagonal gates; the exhaustive planner
-    takes each run, whatever its qudit count, as one segment, and every
-    segment it returns is either within the block limits or all-diagonal."""
+    takes each run, whatever its qudit count, into one segment, alone or
+    behind the generalized Hadamard before it, and every segment it returns
+    is within the block limits, all-diagonal, or a dense part of at most 3
+    qudits and 16 states followed by diagonal gates."""
     dims, gates = wl.circuit_c2(n_qubits=3, n_ququarts=5)
     segs, _ = L.qd_debug_fuse_plan(dims, gates, L.QD_PLAN_EXHAUSTIVE, L.QD_C64, 3, 64)
     assert segs[0][0] == 0 and segs[-1][1] == len(gates) - 1
     assert all(b + 1 == c for (_, b), (c, _) in zip(segs, segs[1:]))
-    long_diag = 0
+    wide = 0
     for a, b in segs:
         qs = {q for g in gates[a:b + 1] for q in tuple(g.targets) + tuple(g.controls or ())}
-        all_diag = all(g.kind in ("Z", "DIAG") for g in gates[a:b + 1])
-        if len(qs) > 3:
-            assert all_diag, (a, b)
-            long_diag += 1
-    assert long_diag >= 1
+        if len(qs) <= 3:
+            continue
+        wide += 1
+        k = b
+        while k >= a and gates[k].kind in ("Z", "DIAG"):
+            k -= 1
+        pre = {q for g in gates[a:k + 1] for q in tuple(g.targets) + tuple(g.controls or ())}
+        assert k < b, (a, b)  # a diagonal suffix
+        assert len(pre) <= 3 and int(np.prod([dims[q] for q in pre])) <= 16, (a, b)
+    assert wide >= 1

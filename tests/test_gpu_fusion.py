@@ -292,4 +292,78 @@ def test_diagonal_runs_match_oracle(prec, case):
         _check(psi, ref, prec)
         seen.update(c.split("_D")[0] for c in _kclasses(dims, gates, prec, kind, 3,
                                                       64 if prec == L.QD_C64 else 32))
-    assert "diag_table" in seen, seen
+    assert "diag_table" in seen or "dense_table" in seen, seen
+    if case == "qft":  # F_d followed by its run of controlled phases: one launch
+        assert "dense_table" in seen, seen
+
+
+@pytest.mark.parametrize("prec", [L.QD_C128, L.QD_C64])
+@pytest.mark.parametrize("dense", ["U1", "U2", "X"])
+def test_dense_part_with_diagonal_run_explicit(prec, dense):
+    """A dense gate (one or two qudits, or a permutation taken as dense)
+    followed by diagonal gates spanning most of the register, planned as one
+    explicit segment: one dense launch with the run's table as epilogue; the
+    state equals the oracle's, on a table range that starts at qudit 0 and on
+    one that starts higher up."""
+    rng = np.random.default_rng(77)
+    dims = [2, 3, 4, 3, 2, 4, 3]
+    N = qo.register_size(dims)
+    for lo in (0, 2):
+        first = {"U1": wl.Gate("U", (3,), matrix=wl.haar_unitary(3, rng)),
+                 "U2": wl.Gate("U", (3, 4), matrix=wl.haar_unitary(6, rng)),
+                 "X": wl.Gate("X", (5,), param=3)}[dense]
+        run = [wl.Gate("Z", (lo,), param=1),
+               wl.Gate("DIAG", (6, lo + 1), matrix=np.exp(2j * np.pi * rng.random(dims[6] * dims[lo + 1]))),
+               wl.Gate("DIAG", (4,), (lo,), (1,), matrix=np.exp(2j * np.pi * rng.random(dims[4]))),
+               wl.Gate("Z", (5,), param=2)]
+        gates = [first] + run
+        psi0 = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+        psi0 /= np.linalg.norm(psi0)
+        ref = qo.run_circuit(dims, gates, psi0=psi0)
+        with L.Register(dims, None, prec) as r:
+            L.qd_set_amplitudes(r.h, psi0)
+            plan = L.qd_plan_create_segmented(r.h, gates, [(0, len(gates) - 1)])
+            names = [L.kclass_name(int(c)) for c in L.qd_plan_timings(plan, with_times=False)[2]]
+            L.qd_plan_run(plan)
+            L.qd_sync(r.h)
+            L.qd_plan_destroy(plan)
+            psi = r.amplitudes().astype(np.complex128)
+        assert len(names) == 1 and names[0].startswith("dense_table"), names
+        _check(psi, ref, prec)
+
+
+@pytest.mark.parametrize("prec", [L.QD_C128, L.QD_C64])
+def test_every_kernel_form_of_a_segment(prec):
+    """One segment with several feasible forms (a dense gate on qudits 1, 2
+    followed by diagonal gates on qudits 1..3: a fused block -- on either
+    block kernel for complex64 -- or a dense part + run).  Each form, forced
+    through qd_plan_create_forms, runs as that kernel class and gives the
+    oracle's state; a form that is not feasible is refused."""
+    rng = np.random.default_rng(91)
+    dims = [2, 3, 3, 2, 4, 3]
+    N = qo.register_size(dims)
+    gates = [wl.Gate("U", (1, 2), matrix=wl.haar_unitary(9, rng)),
+             wl.Gate("Z", (1,), param=1),
+             wl.Gate("DIAG", (3,), (2,), (2,), matrix=np.exp(2j * np.pi * rng.random(2)))]
+    psi0 = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    psi0 /= np.linalg.norm(psi0)
+    ref = qo.run_circuit(dims, gates, psi0=psi0)
+    with L.Register(dims, None, prec) as r:
+        forms = L.qd_segment_forms(r.h, gates, 0, len(gates) - 1)
+        kinds = sorted(k for k, _ in forms)
+        want = [L.QD_FORM_BLOCK] + ([L.QD_FORM_BLOCK_TC] if prec == L.QD_C64 else []) + [L.QD_FORM_DENSE_RUN]
+        assert kinds == want, kinds
+        feat = L.qd_segment_features(r.h, gates, 0, len(gates) - 1)
+        assert int(feat[10]) in kinds
+        for k, f in forms:
+            assert int(f[10]) == k
+            L.qd_set_amplitudes(r.h, psi0)
+            plan = L.qd_plan_create_segmented(r.h, gates, [(0, len(gates) - 1)], [k])
+            names = [L.kclass_name(int(c)) for c in L.qd_plan_timings(plan, with_times=False)[2]]
+            L.qd_plan_run(plan)
+            L.qd_sync(r.h)
+            L.qd_plan_destroy(plan)
+            assert len(names) == 1, names
+            _check(r.amplitudes().astype(np.complex128), ref, prec)
+        with pytest.raises(L.QuditError):
+            L.qd_plan_create_segmented(r.h, gates, [(0, len(gates) - 1)], [L.QD_FORM_DIAG_RUN])  # not all diagonal
