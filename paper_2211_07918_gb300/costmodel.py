@@ -370,15 +370,25 @@ TRAIN_SPECTATORS = (
 )
 
 
-def circuit_samples(n_circuits: int, seed: int = 20000, reps: int = 3, log=None):
+def large_spectators(seed: int, cap: int = 1 << 33):
+    """Spectator ququarts that put the circuit of this seed on a register of
+    2^31..2^33 amplitudes (64-bit index kernels; <= 68.7 GB complex64)."""
+    dims, _ = eval_circuit(seed)
+    k = int(math.floor(math.log(cap / register_size(dims), 4)))
+    return (4,) * max(k, 0)
+
+
+def circuit_samples(n_circuits: int, seed: int = 20000, reps: int = 3, log=None, large: bool = False):
     """Training samples from the planner's own queries: every candidate
     segment of random circuits (the shape of the evaluation circuits, other
-    seeds, varied spectators), each feasible form timed.  Returns X, y."""
+    seeds, varied spectators; large: spectators up to 2^31..2^33
+    amplitudes), each feasible form timed.  Returns X, y."""
     rng = np.random.default_rng(seed)
     X, y = [], []
     t0 = time.time()
     for c in range(n_circuits):
-        spect = TRAIN_SPECTATORS[int(rng.integers(len(TRAIN_SPECTATORS)))]
+        spect = (large_spectators(seed + c) if large
+                 else TRAIN_SPECTATORS[int(rng.integers(len(TRAIN_SPECTATORS)))])
         dims, gates = eval_circuit(seed + c, spectators=spect)
         h = L.qd_create(dims, None, L.QD_C64, 0, 0, 0)
         try:
@@ -389,7 +399,7 @@ def circuit_samples(n_circuits: int, seed: int = 20000, reps: int = 3, log=None)
                 y.append(math.log(max(ms, 1e-4) * 1e3))
         finally:
             L.qd_destroy(h)
-        if log and (c + 1) % 10 == 0:
+        if log and ((c + 1) % 10 == 0 or large):
             log(f"circuits {c + 1}/{n_circuits}: {len(y)} samples, {time.time() - t0:.1f} s")
     return np.array(X, np.float32), np.array(y, np.float32)
 
@@ -437,6 +447,8 @@ def main(argv=None):
                     help="extra samples on registers above 2^31 amplitudes (64-bit index kernels)")
     ap.add_argument("--circuit-samples", type=int, default=0,
                     help="training circuits whose candidate segments are all timed (the planner's own queries)")
+    ap.add_argument("--large-circuit-samples", type=int, default=0,
+                    help="training circuits as --circuit-samples on registers of 2^31..2^33 amplitudes")
     ap.add_argument("--base-data", default=None,
                     help="npz (X, y) of earlier samples to train on together with the new ones")
     args = ap.parse_args(argv)
@@ -461,6 +473,10 @@ def main(argv=None):
         parts_y.append(y)
     if args.circuit_samples > 0:
         X, y = circuit_samples(args.circuit_samples, 20000 + args.seed, log=log)
+        parts_X.append(X)
+        parts_y.append(y)
+    if args.large_circuit_samples > 0:
+        X, y = circuit_samples(args.large_circuit_samples, 30000 + args.seed, reps=2, log=log, large=True)
         parts_X.append(X)
         parts_y.append(y)
     X, y = np.concatenate(parts_X), np.concatenate(parts_y)

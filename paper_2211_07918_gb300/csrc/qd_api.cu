@@ -78,6 +78,7 @@ struct qd_reg {
     int32_t *dev_err = nullptr;
     int64_t tile_stride = -1;  // -1: process default
     int32_t fuse_kmax = 3;     // largest number of qudits of a fused block
+    int32_t index64 = 0;       // 64-bit index kernels below 2^31 amplitudes too
     int32_t fuse_dmax = -1;    // largest dimension of a fused block (-1: 64 for c64, 32 for c128)
     int32_t tc_min_d = 0;      // complex64 fused blocks of D >= this on the tensor cores (0: the cost model decides)
     qd_model *model = nullptr; // learned cost model for QD_PLAN_LEARNED
@@ -135,7 +136,8 @@ int reg_ok(const qd_reg *r) {
 cudaError_t launch_plan(const qd_reg *r, const GatePlan &g) {
     if (g.mode == Mode::Tensor) return launch_block_tc(g, r->psi, r->sm_count, r->dev_err, r->stream);
     if (g.mode == Mode::Table)
-        return diag_table_apply(r->psi, r->prec, (uint64_t)r->N, g.tab_div, g.tab_size, g.tab, r->sm_count, r->stream);
+        return diag_table_apply(r->psi, r->prec, (uint64_t)r->N, g.tab_div, g.tab_size, g.tab, r->sm_count, r->stream,
+                                g.wide);
     if (r->prec == QD_C64) return launch_gate_f32(g, r->psi, r->sm_count, r->stream);
     return launch_gate_f64(g, r->psi, r->sm_count, r->stream);
 }
@@ -283,6 +285,7 @@ int plan_gate(const qd_reg *r, const double *M, const Acting &a, bool diag_only,
     const int D = a.D;
     g.D = D;
     g.N = (uint64_t)r->N;
+    g.wide = r->index64 != 0;
     // matrix / classification
     if (force_dense) {  // the dense kernels, whatever the matrix (a dense part with a table epilogue)
         g.kind = Kind::Dense;
@@ -753,6 +756,10 @@ int qd_set_tuning(qd_reg *r, int32_t key, int64_t value) {
                 return fail(QD_ERR_ARG, "tensor-core block threshold must be 0 (cost model) or in [9, 65]");
             r->tc_min_d = (int32_t)value;
             return QD_OK;
+        case QD_TUNE_INDEX64:
+            if (value != 0 && value != 1) return fail(QD_ERR_ARG, "index width flag must be 0 or 1");
+            r->index64 = (int32_t)value;
+            return QD_OK;
         default:
             return fail(QD_ERR_ARG, "unknown tuning key");
     }
@@ -939,6 +946,7 @@ int plan_block_tc(const qd_reg *r, const FuseBlock &b, GatePlan &g, std::vector<
     g.D = b.D;
     g.Dp = tc_padded_dim(b.D);
     g.N = (uint64_t)r->N;
+    g.wide = r->index64 != 0;
     g.R = (uint64_t)(r->N / b.D);
     std::vector<int> asc(b.qudits.rbegin(), b.qudits.rend());
     std::vector<std::pair<int64_t, int64_t>> ins;
@@ -985,6 +993,7 @@ int plan_diag_run(const qd_reg *r, const std::vector<FuseGate> &fg, int first, i
     g.mode = Mode::Table;
     g.kind = Kind::Mono;
     g.N = (uint64_t)r->N;
+    g.wide = r->index64 != 0;
     g.tab_div = (uint64_t)r->s[qa];
     uint64_t TS = 1;
     spec.range.nr = qb - qa + 1;

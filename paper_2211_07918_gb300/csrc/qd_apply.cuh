@@ -769,7 +769,7 @@ cudaError_t launch_gate_ti(const GatePlan &g, void *psi, int sm_count, cudaStrea
 
 template <typename T>
 cudaError_t launch_gate_t(const GatePlan &g, void *psi, int sm_count, cudaStream_t s) {
-    if (g.N < (uint64_t(1) << 31)) return launch_gate_ti<T, uint32_t>(g, psi, sm_count, s);
+    if (!wide_index(g)) return launch_gate_ti<T, uint32_t>(g, psi, sm_count, s);
     return launch_gate_ti<T, uint64_t>(g, psi, sm_count, s);
 }
 

@@ -34,7 +34,7 @@ struct FastDiv64 {
     uint64_t d;
     uint64_t m;
     uint32_t sh;
-    uint32_t pad;
+    uint32_t p2;  // log2(d) + 1 when d is a power of two (a shift), else 0
 };
 
 inline FastDiv64 make_fastdiv64(uint64_t d) {
@@ -48,6 +48,7 @@ inline FastDiv64 make_fastdiv64(uint64_t d) {
     unsigned __int128 num = (unsigned __int128)1 << f.sh;
     unsigned __int128 m = (num + d - 1) / d;
     f.m = (uint64_t)m;
+    f.p2 = (d & (d - 1)) == 0 ? l + 1 : 0;
     return f;
 }
 
@@ -59,7 +60,10 @@ __host__ __device__ __forceinline__ uint64_t mulhi64(uint64_t a, uint64_t b) {
 #endif
 }
 
+// A power-of-two divisor (every stride of a register of qubits and
+// ququarts) is a shift; the test is uniform across a launch.
 __host__ __device__ __forceinline__ uint64_t fdiv(uint64_t n, const FastDiv64 &f) {
+    if (f.p2) return n >> (f.p2 - 1);
     const uint64_t hi = mulhi64(n, f.m);
     const uint64_t lo = n * f.m;
     return f.sh >= 64 ? (hi >> (f.sh - 64)) : ((hi << (64 - f.sh)) | (lo >> f.sh));

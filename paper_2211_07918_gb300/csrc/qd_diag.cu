@@ -146,10 +146,10 @@ cudaError_t diag_table_build(void *tab, int prec, uint64_t TS, const DiagRange &
 }
 
 cudaError_t diag_table_apply(void *psi, int prec, uint64_t N, uint64_t s_qa, uint64_t TS, const void *tab,
-                             int sm_count, cudaStream_t s) {
+                             int sm_count, cudaStream_t s, bool wide) {
     const int grid = grid_for(N, 4, sm_count);
     if (grid <= 0) return cudaSuccess;
-    if (N < (uint64_t(1) << 31)) {
+    if (N < (uint64_t(1) << 31) && !wide) {
         const FastDiv32 a = make_fastdiv32((uint32_t)s_qa), t = make_fastdiv32((uint32_t)TS);
         if (prec == 1)
             k_diag_apply_f32<uint32_t><<<grid, kDiagBlock, 0, s>>>(static_cast<float2 *>(psi), (uint32_t)N, a, t,

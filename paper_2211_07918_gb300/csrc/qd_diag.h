@@ -30,8 +30,9 @@ struct DiagGateDesc {
 cudaError_t diag_table_build(void *tab, int prec, uint64_t TS, const DiagRange &rg, const DiagGateDesc *gates_dev,
                              int32_t ngates, const double2 *pool_dev, int sm_count, cudaStream_t s);
 
-// psi[i] *= tab[(i / s_qa) mod TS] for every i < N.
+// psi[i] *= tab[(i / s_qa) mod TS] for every i < N (wide: 64-bit index
+// arithmetic below 2^31 amplitudes too).
 cudaError_t diag_table_apply(void *psi, int prec, uint64_t N, uint64_t s_qa, uint64_t TS, const void *tab,
-                             int sm_count, cudaStream_t s);
+                             int sm_count, cudaStream_t s, bool wide = false);
 
 }  // namespace qd

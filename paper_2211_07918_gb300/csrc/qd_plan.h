@@ -28,6 +28,7 @@ struct GatePlan {
     Kind kind = Kind::Dense;
     int32_t D = 0;
     uint64_t N = 0;  // register size (selects 32- or 64-bit index arithmetic)
+    bool wide = false;  // 64-bit index arithmetic below 2^31 too (QD_TUNE_INDEX64)
 
     // --- direct mode: one thread per group --------------------------------
     uint64_t R = 0;          // number of groups
@@ -69,6 +70,10 @@ struct GatePlan {
     // --- accounting --------------------------------------------------------
     double alg_bytes = 0;  // algorithmic HBM bytes of one launch
 };
+
+// 64-bit index kernels: registers of 2^31 amplitudes or more (FastDiv32's
+// dividend bound), or any register when asked for.
+inline bool wide_index(const GatePlan &g) { return g.wide || g.N >= (uint64_t(1) << 31); }
 
 // Per-precision launchers (qd_apply_f32.cu / qd_apply_f64.cu).
 cudaError_t launch_gate_f32(const GatePlan &g, void *psi, int sm_count, cudaStream_t s);

@@ -622,7 +622,7 @@ static cudaError_t launch_tc_i(const GatePlan &g, void *psi, int sm_count, int32
 }
 
 cudaError_t launch_block_tc(const GatePlan &g, void *psi, int sm_count, int32_t *err, cudaStream_t s) {
-    if (g.N < (uint64_t(1) << 31)) return launch_tc_i<uint32_t>(g, psi, sm_count, err, s);
+    if (!wide_index(g)) return launch_tc_i<uint32_t>(g, psi, sm_count, err, s);
     return launch_tc_i<uint64_t>(g, psi, sm_count, err, s);
 }
 

@@ -23,7 +23,7 @@ QD_GATE_X, QD_GATE_Z, QD_GATE_H, QD_GATE_U, QD_GATE_DIAG, QD_GATE_MEASURE = 1, 2
 QD_OUT_AMPLITUDE, QD_OUT_PROBABILITY = 0, 1
 QD_PLAN_NONE, QD_PLAN_GREEDY, QD_PLAN_LEARNED, QD_PLAN_EXHAUSTIVE = 0, 1, 2, 3
 QD_MAX_TARGETS, QD_MAX_CONTROLS = 6, 8
-QD_TUNE_TILE_STRIDE, QD_TUNE_FUSE_KMAX, QD_TUNE_FUSE_DMAX, QD_TUNE_TC_MIN_D = 1, 2, 3, 4
+QD_TUNE_TILE_STRIDE, QD_TUNE_FUSE_KMAX, QD_TUNE_FUSE_DMAX, QD_TUNE_TC_MIN_D, QD_TUNE_INDEX64 = 1, 2, 3, 4, 5
 # kernel forms of one launch (launch feature 10)
 QD_FORM_MONO, QD_FORM_DENSE, QD_FORM_BLOCK, QD_FORM_BLOCK_TC, QD_FORM_DIAG_RUN, QD_FORM_DENSE_RUN = range(6)
 QD_MODEL_FEATURES, QD_MODEL_PARAMS = 12, 9217

@@ -19,8 +19,10 @@ def _built():
     L.load()
 
 
-def _run(dims, gates, prec, kind, psi0=None, kmax=None, dmax=None, tc_min_d=None):
+def _run(dims, gates, prec, kind, psi0=None, kmax=None, dmax=None, tc_min_d=None, index64=False):
     with L.Register(dims, None, prec) as r:
+        if index64:
+            L.qd_set_tuning(r.h, L.QD_TUNE_INDEX64, 1)
         if tc_min_d:
             L.qd_set_tuning(r.h, L.QD_TUNE_TC_MIN_D, tc_min_d)
         if kmax:
@@ -367,3 +369,47 @@ def test_every_kernel_form_of_a_segment(prec):
             _check(r.amplitudes().astype(np.complex128), ref, prec)
         with pytest.raises(L.QuditError):
             L.qd_plan_create_segmented(r.h, gates, [(0, len(gates) - 1)], [L.QD_FORM_DIAG_RUN])  # not all diagonal
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_fused_plans_on_64bit_index_kernels(seed):
+    """Fused plans (blocks on both dense kernels, diagonal runs, dense parts
+    with a run, mono blocks) with the 64-bit index kernels forced on small
+    registers; even seeds use qubits and ququarts only (every stride a power
+    of two, every division a shift), odd seeds dims 2..5.  Every amplitude
+    against the oracle."""
+    rng = np.random.default_rng(1500 + seed)
+    n = int(rng.integers(5, 9))
+    dims = [int(x) for x in rng.choice([2, 4] if seed % 2 == 0 else [2, 3, 4, 5], size=n)]
+    while qo.register_size(dims) > 120000:
+        dims.pop()
+    gates = wl.random_circuit(dims, 40, 1500 + seed, wl.C0_MIX + ("U2",))
+    gates += _diag_heavy_circuit(dims, 20, 1500 + seed)
+    gates = [g for g in gates if np.prod([dims[q] for q in g.targets]) <= 32]
+    N = qo.register_size(dims)
+    psi0 = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    psi0 /= np.linalg.norm(psi0)
+    ref = qf.run_circuit(dims, gates, psi0=psi0)
+    for prec in (L.QD_C128, L.QD_C64):
+        for kind in (L.QD_PLAN_NONE, L.QD_PLAN_GREEDY, L.QD_PLAN_EXHAUSTIVE):
+            for tc_min_d in ((None, 9, 65) if prec == L.QD_C64 and kind == L.QD_PLAN_EXHAUSTIVE else (None,)):
+                psi, info = _run(dims, gates, prec, kind, psi0=psi0, kmax=3,
+                                 dmax=64 if prec == L.QD_C64 else 32, tc_min_d=tc_min_d, index64=True)
+                _check(psi, ref, prec)
+
+
+def test_qft_runs_on_64bit_index_kernels():
+    """The QFT + ladder shape (F_d followed by its run of controlled phases:
+    dense part + run launches, tables from qudit 8 up) on 3 qubits + 5
+    ququarts with the 64-bit index kernels forced."""
+    dims, gates = wl.circuit_c2(n_qubits=3, n_ququarts=5)
+    N = qo.register_size(dims)
+    rng = np.random.default_rng(4)
+    psi0 = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    psi0 /= np.linalg.norm(psi0)
+    ref = qf.run_circuit(dims, gates, psi0=psi0)
+    for prec in (L.QD_C128, L.QD_C64):
+        for kind in (L.QD_PLAN_GREEDY, L.QD_PLAN_EXHAUSTIVE):
+            psi, info = _run(dims, gates, prec, kind, psi0=psi0, kmax=3, dmax=64 if prec == L.QD_C64 else 32,
+                             index64=True)
+            _check(psi, ref, prec)

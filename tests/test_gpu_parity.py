@@ -31,8 +31,10 @@ def _built():
     L.load()
 
 
-def run_gpu(dims, gates, prec, init=None, psi0=None, plan=L.QD_PLAN_NONE, tile_stride=None):
+def run_gpu(dims, gates, prec, init=None, psi0=None, plan=L.QD_PLAN_NONE, tile_stride=None, index64=False):
     with L.Register(dims, init, prec, tile_stride=tile_stride) as r:
+        if index64:
+            L.qd_set_tuning(r.h, L.QD_TUNE_INDEX64, 1)
         if psi0 is not None:
             L.qd_set_amplitudes(r.h, psi0)
         r.run(gates, plan)
@@ -115,9 +117,10 @@ def test_c0_per_gate_and_norm(prec):
 
 # ------------------------------------------------- random sweep of geometries
 
-def _random_case(rng, nmax=8, Nmax=60000):
+def _random_case(rng, nmax=8, Nmax=60000, pow2=False):
     n = int(rng.integers(1, nmax + 1))
-    dims = [int(x) for x in rng.integers(2, 8, size=n)]
+    dims = ([int(x) for x in rng.choice([2, 4], size=n)] if pow2
+            else [int(x) for x in rng.integers(2, 8, size=n)])
     while qo.register_size(dims) > Nmax:
         dims.pop()
     n = len(dims)
@@ -158,6 +161,22 @@ def test_random_geometry_sweep(seed, prec, tile_stride):
     psi0 = rand_state(rng, qo.register_size(dims))
     ref = qf.run_circuit(dims, gates, psi0=psi0)
     psi = run_gpu(dims, gates, prec, psi0=psi0, tile_stride=tile_stride)
+    check(psi, ref, prec)
+
+
+@pytest.mark.parametrize("tile_stride", [0, 32])
+@pytest.mark.parametrize("seed", range(12))
+@pytest.mark.parametrize("prec", [L.QD_C128, L.QD_C64])
+def test_random_geometry_sweep_index64(seed, prec, tile_stride):
+    """The 64-bit index kernels (those of registers of >= 2^31 amplitudes,
+    power-of-two divisors as shifts) forced on small registers, so that
+    every amplitude is compared with the oracle; seeds 700+ draw dims in
+    {2, 4} half of the time (all strides powers of two)."""
+    rng = np.random.default_rng(700 + seed)
+    dims, gates = _random_case(rng, pow2=seed % 2 == 0)
+    psi0 = rand_state(rng, qo.register_size(dims))
+    ref = qf.run_circuit(dims, gates, psi0=psi0)
+    psi = run_gpu(dims, gates, prec, psi0=psi0, tile_stride=tile_stride, index64=True)
     check(psi, ref, prec)
 
 
