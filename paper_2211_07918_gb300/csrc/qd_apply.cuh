@@ -92,6 +92,10 @@ inline unsigned long long pk_host(float a, float b) {
 }
 // Dense complex64 gates of up to 4 x 4 use the packed path.
 template <typename T, int MD> constexpr bool kPacked = kSplit<T> && MD <= 4;
+// Kernels with a contiguous-members path (complex64, even member bound):
+// a gate on the lowest qudits, whose group is D consecutive amplitudes
+// starting at a multiple of D, reads and writes 16-byte amplitude pairs.
+template <typename T, int MD> constexpr bool kVecPairs = kSplit<T> && MD % 2 == 0 && MD <= 16;
 
 template <typename T>
 inline void split_coef(double re, double im, v2<T> &hi, v2<T> &lo) {
@@ -108,6 +112,7 @@ struct DenseDirectArgs {
     v2<T> *psi;
     I R, base;
     int32_t D;
+    int32_t contig;  // members at offsets 0..D-1 (D == MD): 16-byte amplitude-pair accesses
     ExpandT<I> ex;
     I off[MD];
     v2<T> U[MD * MD];  // row-major, zero-padded to MD x MD
@@ -199,11 +204,39 @@ __global__ void __launch_bounds__(256, (direct_min_blocks<T, MD, true>())) k_den
             ok[u] = r < a.R;
             base[u] = ok[u] ? expand(r, a.ex) + a.base : 0;
         }
+        const bool pairs = kVecPairs<T, MD> && a.contig;
 #pragma unroll
-        for (int u = 0; u < UN; ++u)
+        for (int u = 0; u < UN; ++u) {
+            if constexpr (kVecPairs<T, MD>) {
+                if (pairs) {
+                    const float4 *p = reinterpret_cast<const float4 *>(a.psi + base[u]);
+#pragma unroll
+                    for (int h = 0; h < MD / 2; ++h) {
+                        const float4 q = ok[u] ? p[h] : make_float4(0.f, 0.f, 0.f, 0.f);
+                        v[u][2 * h] = mk<T>(q.x, q.y);
+                        v[u][2 * h + 1] = mk<T>(q.z, q.w);
+                    }
+                    continue;
+                }
+            }
 #pragma unroll
             for (int j = 0; j < MD; ++j)
                 v[u][j] = (ok[u] && (EX || j < D)) ? a.psi[base[u] + a.off[j]] : mk<T>(T(0), T(0));
+        }
+        // output i of group u: with amplitude pairs, odd outputs store the pair
+        v2<T> prev = mk<T>(T(0), T(0));
+        auto put = [&](int u, int i, const v2<T> o) {
+            if constexpr (kVecPairs<T, MD>) {
+                if (pairs) {
+                    if (i & 1)
+                        reinterpret_cast<float4 *>(a.psi + base[u])[i / 2] = make_float4(prev.x, prev.y, o.x, o.y);
+                    else
+                        prev = o;
+                    return;
+                }
+            }
+            a.psi[base[u] + a.off[i]] = o;
+        };
         if constexpr (kPacked<T, MD>) {
             // lo terms first, then hi terms (as below), two lanes per FMA
 #pragma unroll
@@ -230,7 +263,7 @@ __global__ void __launch_bounds__(256, (direct_min_blocks<T, MD, true>())) k_den
                             acc = pk_fma(a.Pk[4 * (i * MD + j) + 3], ps[j], acc);
                         }
                         const float2 o = pk_unpack(acc);
-                        a.psi[base[u] + a.off[i]] = mk<T>(o.x, o.y);
+                        put(u, i, mk<T>(o.x, o.y));
                     }
                 }
             }
@@ -248,7 +281,7 @@ __global__ void __launch_bounds__(256, (direct_min_blocks<T, MD, true>())) k_den
                     }
 #pragma unroll
                     for (int j = 0; j < MD; ++j) cmac<T>(acc, a.U[i * MD + j], v[u][j]);
-                    a.psi[base[u] + a.off[i]] = acc;
+                    put(u, i, acc);
                 }
             }
         }
@@ -302,7 +335,9 @@ struct DenseTableArgs {
     DenseDirectArgs<T, I, MD> d;
     typename DivOfI<I>::type divA, divT;  // by s_qa and by TS
     uint32_t oq[MD];  // (off_j / s_qa) mod TS
-    I orm[MD];        // off_j mod s_qa
+    I thr[MD];        // s_qa - off_j mod s_qa: member j's carry iff b mod s_qa >= thr_j
+    uint32_t carry;   // some off_j is not a multiple of s_qa
+    uint32_t tsmask;  // TS - 1 when TS is a power of two, else 0
     const typename TabEntry<T>::type *tab;
 };
 
@@ -318,7 +353,8 @@ __device__ __forceinline__ v2<T> times_entry(const v2<T> o, const typename TabEn
 // Two groups per thread per iteration for up to four members.  The table
 // index of member j of a group at base b is, with b = qb s_qa + rb,
 // (qb + off_j / s_qa + [rb + off_j mod s_qa >= s_qa]) mod TS (< 2^24): two
-// divisions per group instead of two per member.  The table entries of a
+// divisions per group instead of two per member (none when every member
+// offset is a multiple of s_qa, a mask when TS is a power of two).  The table entries of a
 // group's outputs are loaded before the first of them is stored (a load
 // after a store to the state could not be moved above it, and each output
 // would wait out its own table latency): all of them for up to four
@@ -361,8 +397,7 @@ __global__ void __launch_bounds__(256, (table_min_blocks<T, I, MD>()))
             if (!ok[u]) continue;
             // the group's table position (while its member loads are in flight)
             const I qb = fdiv(base[u], a.divA);
-            const I rb = base[u] - qb * sA;
-            const uint32_t kb = (uint32_t)(qb - fdiv(qb, a.divT) * (I)TS);
+            const uint32_t kb = a.tsmask ? (uint32_t)qb & a.tsmask : (uint32_t)(qb - fdiv(qb, a.divT) * (I)TS);
 #pragma unroll
             for (int c0 = 0; c0 < MD; c0 += TB) {
                 Entry t[TB];
@@ -370,9 +405,14 @@ __global__ void __launch_bounds__(256, (table_min_blocks<T, I, MD>()))
                 for (int c = 0; c < TB; ++c) {
                     const int i = c0 + c;
                     if (EX || i < D) {
-                        uint32_t k = kb + a.oq[i] + (rb + a.orm[i] >= sA ? 1u : 0u);
-                        if (k >= TS) k -= TS;
-                        if (k >= TS) k -= TS;
+                        uint32_t k = kb + a.oq[i];  // < 2 TS
+                        if (a.carry && base[u] - qb * sA >= a.thr[i]) ++k;
+                        if (a.tsmask) {
+                            k &= a.tsmask;
+                        } else {
+                            if (k >= TS) k -= TS;
+                            if (k >= TS) k -= TS;
+                        }
                         t[c] = __ldg(&a.tab[k]);
                     }
                 }
@@ -633,6 +673,34 @@ cudaError_t launch_dense(const GatePlan &g, void *psi, int sm_count, cudaStream_
         a.ex = expand_for<I>(g.ex);
         for (int j = 0; j < MD; ++j) a.off[j] = j < g.D ? (I)g.off[j] : 0;
         fill_matrix<T, MD>(a.U, a.Ulo, g);
+        a.contig = 0;
+        if constexpr (kVecPairs<T, MD>) {
+            // a group of D == MD consecutive amplitudes (the gate acts on the
+            // lowest qudits): relabel the local basis in address order (rows
+            // and columns of U alike) and move amplitude pairs
+            int perm[MD];
+            bool contig = g.D == MD;
+            for (int j = 0; j < MD && contig; ++j) {
+                perm[j] = -1;
+                for (int m = 0; m < MD; ++m)
+                    if (g.off[m] == j) perm[j] = m;
+                contig = perm[j] >= 0;
+            }
+            if (contig) {
+                v2<T> U2[MD * MD], L2[MD * MD];
+                for (int i = 0; i < MD; ++i)
+                    for (int j = 0; j < MD; ++j) {
+                        U2[i * MD + j] = a.U[perm[i] * MD + perm[j]];
+                        L2[i * MD + j] = a.Ulo[perm[i] * MD + perm[j]];
+                    }
+                for (int k = 0; k < MD * MD; ++k) {
+                    a.U[k] = U2[k];
+                    a.Ulo[k] = L2[k];
+                }
+                for (int j = 0; j < MD; ++j) a.off[j] = (I)j;
+                a.contig = 1;
+            }
+        }
         fill_packed<T, I, MD>(a);
         auto fn = k_dense_direct<T, I, MD, EX>;
         const int grid = grid_of(g.R, kBlock, sm_count, occupancy_blocks((const void *)fn, kBlock, 0));
@@ -710,6 +778,7 @@ cudaError_t launch_dense_table(const GatePlan &g, void *psi, int sm_count, cudaS
     a.d.R = (I)g.R;
     a.d.base = (I)g.base_off;
     a.d.D = g.D;
+    a.d.contig = 0;
     a.d.ex = expand_for<I>(g.ex);
     for (int j = 0; j < MD; ++j) a.d.off[j] = j < g.D ? (I)g.off[j] : 0;
     fill_matrix<T, MD>(a.d.U, a.d.Ulo, g);
@@ -721,11 +790,14 @@ cudaError_t launch_dense_table(const GatePlan &g, void *psi, int sm_count, cudaS
         a.divA = make_fastdiv64(g.tab_div);
         a.divT = make_fastdiv64(g.tab_size);
     }
+    a.carry = 0;
     for (int j = 0; j < MD; ++j) {
         const uint64_t o = j < g.D ? (uint64_t)g.off[j] : 0;
         a.oq[j] = (uint32_t)((o / g.tab_div) % g.tab_size);
-        a.orm[j] = (I)(o % g.tab_div);
+        a.thr[j] = (I)(g.tab_div - o % g.tab_div);
+        if (o % g.tab_div) a.carry = 1;
     }
+    a.tsmask = (g.tab_size & (g.tab_size - 1)) == 0 ? (uint32_t)(g.tab_size - 1) : 0u;
     a.tab = static_cast<const typename TabEntry<T>::type *>(g.tab);
     auto fn = k_dense_table<T, I, MD, EX>;
     const int grid = grid_of(g.R, kBlock, sm_count, occupancy_blocks((const void *)fn, kBlock, 0));

@@ -481,24 +481,36 @@ __global__ void __launch_bounds__(TcCfg<MAXD>::THREADS, 1) k_block_tc(const __gr
             if (!ws_wait(smem_u32(&acc_full[sl]), (uint32_t)(i / C::SLOTS) & 1u, &abort_flag, a.err)) break;
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
             const uint32_t lane_addr = tmem + (uint32_t)sl * (uint32_t)C::NACC * Nc + ((uint32_t)(warp * 32) << 16);
+            // 16 amplitudes (32 columns of each accumulator) per TMEM wait: the
+            // four loads are in flight together
 #pragma unroll
-            for (int c0 = 0; c0 < MAXD; c0 += 8) {  // 8 amplitudes = 16 columns per accumulator
+            for (int c0 = 0; c0 < MAXD; c0 += 16) {
                 if (c0 < a.Dp) {
-                    uint32_t l0[16], l1[16];
-                    tmem_ld16_nowait(lane_addr + (uint32_t)(2 * c0), l0);
-                    tmem_ld16_nowait(lane_addr + Nc + (uint32_t)(2 * c0), l1);
+                    uint32_t l0[2][16], l1[2][16];
+                    tmem_ld16_nowait(lane_addr + (uint32_t)(2 * c0), l0[0]);
+                    tmem_ld16_nowait(lane_addr + Nc + (uint32_t)(2 * c0), l1[0]);
+                    const bool second = c0 + 8 < a.Dp;
+                    if (second) {
+                        tmem_ld16_nowait(lane_addr + (uint32_t)(2 * (c0 + 8)), l0[1]);
+                        tmem_ld16_nowait(lane_addr + Nc + (uint32_t)(2 * (c0 + 8)), l1[1]);
+                    }
                     tmem_wait_ld();
                     if (valid) {
 #pragma unroll
-                        for (int uu = 0; uu < 8; ++uu) {
-                            const int j = c0 + uu;
-                            if (j < a.D) {
-                                const int n = 2 * j;
-                                const float re = (__uint_as_float(l0[2 * uu]) + __uint_as_float(l1[2 * uu])) *
-                                                 (escale * bscale[n]);
-                                const float im = (__uint_as_float(l0[2 * uu + 1]) + __uint_as_float(l1[2 * uu + 1])) *
-                                                 (escale * bscale[n + 1]);
-                                a.psi[base + a.off[j]] = make_float2(re, im);
+                        for (int hh = 0; hh < 2; ++hh) {
+#pragma unroll
+                            for (int uu = 0; uu < 8; ++uu) {
+                                const int j = c0 + 8 * hh + uu;
+                                if (j < a.D) {
+                                    const int n = 2 * j;
+                                    const float re =
+                                        (__uint_as_float(l0[hh][2 * uu]) + __uint_as_float(l1[hh][2 * uu])) *
+                                        (escale * bscale[n]);
+                                    const float im =
+                                        (__uint_as_float(l0[hh][2 * uu + 1]) + __uint_as_float(l1[hh][2 * uu + 1])) *
+                                        (escale * bscale[n + 1]);
+                                    a.psi[base + a.off[j]] = make_float2(re, im);
+                                }
                             }
                         }
                     }

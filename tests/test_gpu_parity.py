@@ -180,6 +180,29 @@ def test_random_geometry_sweep_index64(seed, prec, tile_stride):
     check(psi, ref, prec)
 
 
+@pytest.mark.parametrize("index64", [False, True])
+@pytest.mark.parametrize("prec", [L.QD_C128, L.QD_C64])
+def test_dense_gates_on_the_lowest_qudits(prec, index64):
+    """Dense gates whose group is D consecutive amplitudes (targets = the
+    lowest qudits, in any listed order, D even: the complex64 kernels move
+    16-byte amplitude pairs) with and without controls above them; every
+    amplitude against the oracle."""
+    rng = np.random.default_rng(61)
+    dims = [2, 4, 2, 3, 2, 5, 2]
+    N = qo.register_size(dims)
+    gates = []
+    for t in [(0,), (1, 0), (0, 1), (2, 1, 0), (1, 2, 0), (0, 2, 1)]:
+        D = int(np.prod([dims[q] for q in t]))
+        gates.append(Gate("U", t, matrix=wl.haar_unitary(D, rng)))
+        gates.append(Gate("U", t, (4, 5), (1, 3), matrix=wl.haar_unitary(D, rng)))
+    gates.append(Gate("U", (1,), matrix=wl.haar_unitary(4, rng)))       # stride 2: not contiguous
+    gates.append(Gate("U", (0, 2), matrix=wl.haar_unitary(4, rng)))     # offsets 0, 1, 8, 9
+    psi0 = rand_state(rng, N)
+    ref = qf.run_circuit(dims, gates, psi0=psi0)
+    psi = run_gpu(dims, gates, prec, psi0=psi0, index64=index64)
+    check(psi, ref, prec)
+
+
 @pytest.mark.parametrize("prec", [L.QD_C128, L.QD_C64])
 def test_controlled_leaves_other_levels_bit_identical(prec):
     rng = np.random.default_rng(9)
