@@ -173,6 +173,10 @@ template <int MAXD> struct TcCfg {
     static constexpr int THREADS = 32 * (5 + PW);
     static constexpr int NPAIRS = 6;
     static constexpr bool PRE = MAXD <= 32;  // slices built before the stage is free
+    // Above D = 32 the single stage is written in two K halves, each by the
+    // threads that hold its amplitudes (part 0: amplitudes 0..31, part 1:
+    // the rest) and released by the MMAs of that half alone: while one half's
+    // MMAs run, the other half of the next tile is sliced and stored.
     // Stage-release barriers: tile i's MMAs commit to empty[i % NE]; the
     // writer of tile i waits for tile i - STAGES on empty[(i - STAGES) % NE].
     // With one stage NE = 2 (one barrier per tile parity): should two
@@ -253,7 +257,13 @@ __global__ void __launch_bounds__(TcCfg<MAXD>::THREADS, 1) k_block_tc(const __gr
     const float *bscale = reinterpret_cast<const float *>(B + 3u * bbytes);
     const uint32_t bregion = (3u * bbytes + K * 4u + 1023u) & ~1023u;
     unsigned char *stages = sm + bregion;  // stage s: X1 | X2 | X3 at s * XS * xbytes
-    __shared__ __align__(8) uint64_t full[C::STAGES], empty[C::NE], acc_full[C::SLOTS], acc_empty[C::SLOTS];
+    // full / empty: one barrier per stage (and K half, above D = 32)
+    __shared__ __align__(8) uint64_t full[C::STAGES * C::TPR], empty[C::NE * C::TPR], acc_full[C::SLOTS],
+        acc_empty[C::SLOTS];
+    // above D = 32: the two halves of a row exchange their maxima through
+    // shared memory (a 2-deep ring, one barrier per slot)
+    __shared__ __align__(8) uint64_t xm_full[2];
+    __shared__ float xmax[2][2][kTcRows];
     // row scales of a tile: a 2-deep ring between producers and epilogue
     __shared__ __align__(8) uint64_t sc_full[2], sc_empty[2];
     __shared__ int32_t erow[2][kTcRows];
@@ -272,12 +282,15 @@ __global__ void __launch_bounds__(TcCfg<MAXD>::THREADS, 1) k_block_tc(const __gr
         for (uint32_t i = tid; i < n16; i += blockDim.x) dst[i] = src[i];
     }
     if (tid == 0) {
-        for (int q = 0; q < C::STAGES; ++q)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&full[q])), "r"(kTcRows * C::TPR)
+        for (int q = 0; q < C::STAGES * C::TPR; ++q)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&full[q])), "r"(kTcRows)
                          : "memory");
-        // a stage is free once the MMAs reading it have completed (tcgen05.commit)
-        for (int q = 0; q < C::NE; ++q)
+        // a stage (half) is free once the MMAs reading it have completed (tcgen05.commit)
+        for (int q = 0; q < C::NE * C::TPR; ++q)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&empty[q])) : "memory");
+        for (int q = 0; q < 2; ++q)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&xm_full[q])), "r"(2 * kTcRows)
+                         : "memory");
         for (int q = 0; q < C::SLOTS; ++q) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&acc_full[q])) : "memory");
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&acc_empty[q])), "r"(kTcRows)
@@ -312,7 +325,9 @@ __global__ void __launch_bounds__(TcCfg<MAXD>::THREADS, 1) k_block_tc(const __gr
         const int p = tid - 160;
         const int grp = p / (kTcRows * C::TPR);
         const int q = p % (kTcRows * C::TPR);
-        const int row = q / C::TPR, part = q % C::TPR;  // this thread's amplitudes: [part RA, (part + 1) RA)
+        // this thread's amplitudes: [part RA, (part + 1) RA) of its row; the
+        // two parts of the rows are in different warps
+        const int row = q % kTcRows, part = q / kTcRows;
         const int j0 = part * C::RA;
         for (I i = (I)grp; i < nlocal; i += NGRP) {
             const int st = (int)(i % C::STAGES);
@@ -339,7 +354,17 @@ __global__ void __launch_bounds__(TcCfg<MAXD>::THREADS, 1) k_block_tc(const __gr
             float amax = 0.f;
 #pragma unroll
             for (int j = 0; j < C::RA; ++j) amax = fmaxf(amax, fmaxf(fabsf(v[j].x), fabsf(v[j].y)));
-            if constexpr (C::TPR == 2) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, 1));
+            if constexpr (C::TPR == 2) {
+                const int xs = (int)(i & 1);
+                xmax[xs][part][row] = amax;
+                mbar_arrive(smem_u32(&xm_full[xs]));
+                // a slot is rewritten two tiles later, after every thread has
+                // passed the next exchange (and so has read this one)
+                bool okx = ws_wait(smem_u32(&xm_full[xs]), (uint32_t)(i >> 1) & 1u, &abort_flag, a.err);
+                okx = __all_sync(0xffffffffu, okx);
+                if (!okx) break;
+                amax = fmaxf(xmax[xs][0][row], xmax[xs][1][row]);
+            }
             int e = 0;
             frexpf(amax, &e);  // amax <= 2^e
             const f2p inv2 = pk2(ldexpf(1.0f, -e), ldexpf(1.0f, -e));
@@ -374,8 +399,9 @@ __global__ void __launch_bounds__(TcCfg<MAXD>::THREADS, 1) k_block_tc(const __gr
             }
             bool ok = true;
             if (i >= (I)C::STAGES) {
-                const I wt = i - (I)C::STAGES;  // the tile whose MMAs last read this stage
-                ok = ws_wait(smem_u32(&empty[(int)(wt % C::NE)]), (uint32_t)(wt / C::NE) & 1u, &abort_flag, a.err);
+                const I wt = i - (I)C::STAGES;  // the tile whose MMAs last read this stage (half)
+                ok = ws_wait(smem_u32(&empty[(int)(wt % C::NE) * C::TPR + part]), (uint32_t)(wt / C::NE) & 1u,
+                             &abort_flag, a.err);
             }
             if constexpr (C::TPR == 2) ok = __all_sync(0xffffffffu, ok);
             if (!ok) break;
@@ -404,7 +430,7 @@ __global__ void __launch_bounds__(TcCfg<MAXD>::THREADS, 1) k_block_tc(const __gr
                 }
             }
             asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-            mbar_arrive(smem_u32(&full[st]));
+            mbar_arrive(smem_u32(&full[st * C::TPR + part]));
         }
     } else if (warp == 4) {
         // ------------------------------------------------------------ MMA issuer
@@ -417,10 +443,17 @@ __global__ void __launch_bounds__(TcCfg<MAXD>::THREADS, 1) k_block_tc(const __gr
             // each accumulator starts it
             const int pairs[6][3] = {{0, 0, 0}, {1, 0, 1}, {1, 1, 0}, {1, 0, 2}, {1, 1, 1}, {1, 2, 0}};
             const uint32_t ksteps = K / 16u;
-            I issued = 0, released = 0;
-            for (I i = 0; i < nlocal; ++i) {
+            // K steps of the first half: the columns of part 0's amplitudes
+            const uint32_t khalf = C::TPR == 2 ? std::min<uint32_t>(ksteps, (uint32_t)(2 * C::RA / 16)) : ksteps;
+            // the most recent commit: once it has arrived, every MMA issued
+            // before it has completed
+            uint32_t last_mb = 0, last_par = 0;
+            bool any = false;
+            bool good = true;
+            for (I i = 0; i < nlocal && good; ++i) {
                 const int st = (int)(i % C::STAGES);
-                if (!ws_wait(smem_u32(&full[st]), (uint32_t)(i / C::STAGES) & 1u, &abort_flag, a.err)) break;
+                const uint32_t fpar = (uint32_t)(i / C::STAGES) & 1u;
+                if (!ws_wait(smem_u32(&full[st * C::TPR]), fpar, &abort_flag, a.err)) break;
                 const int sl = (int)(i % C::SLOTS);
                 if (i >= (I)C::SLOTS &&
                     !ws_wait(smem_u32(&acc_empty[sl]), (uint32_t)(i / C::SLOTS - 1) & 1u, &abort_flag, a.err))
@@ -432,36 +465,41 @@ __global__ void __launch_bounds__(TcCfg<MAXD>::THREADS, 1) k_block_tc(const __gr
                 // operands by 256 bytes, i.e. 16 in the descriptors' address field
                 // (shared addresses stay below 2^18, so the field does not overflow)
 #pragma unroll
-                for (int pp = 0; pp < C::NPAIRS; ++pp) {
-                    const uint32_t dcol = acc + (uint32_t)pairs[pp][0] * Nc;
-                    const uint32_t xa = x0 + (uint32_t)pairs[pp][1] * xbytes;
-                    const uint32_t bt = b0 + (uint32_t)pairs[pp][2] * bbytes;
-                    const bool first_of_acc = (pp == 0 || pp == 1);
-                    const uint64_t da = smem_desc(xa, lbo, sbo), db = smem_desc(bt, lbo, sbo);
-                    mma_bf16(dcol, da, db, idesc, first_of_acc ? 0u : 1u);
+                for (int h = 0; h < C::TPR; ++h) {
+                    const uint32_t k_lo = h == 0 ? 0u : khalf, k_hi = h == 0 ? khalf : ksteps;
+                    if (h == 1) {
+                        // the second half of the stage, written by part 1
+                        if (!ws_wait(smem_u32(&full[st * C::TPR + 1]), fpar, &abort_flag, a.err)) {
+                            good = false;
+                            break;
+                        }
+                        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                    }
+#pragma unroll
+                    for (int pp = 0; pp < C::NPAIRS; ++pp) {
+                        const uint32_t dcol = acc + (uint32_t)pairs[pp][0] * Nc;
+                        const uint32_t xa = x0 + (uint32_t)pairs[pp][1] * xbytes;
+                        const uint32_t bt = b0 + (uint32_t)pairs[pp][2] * bbytes;
+                        const bool first_of_acc = h == 0 && (pp == 0 || pp == 1);
+                        const uint64_t da = smem_desc(xa, lbo, sbo), db = smem_desc(bt, lbo, sbo);
 #pragma unroll 1
-                    for (uint32_t ks = 1; ks < ksteps; ++ks)
-                        mma_bf16(dcol, da + (uint64_t)(ks * 16u), db + (uint64_t)(ks * 16u), idesc, 1u);
+                        for (uint32_t ks = k_lo; ks < k_hi; ++ks)
+                            mma_bf16(dcol, da + (uint64_t)(ks * 16u), db + (uint64_t)(ks * 16u), idesc,
+                                     (first_of_acc && ks == 0) ? 0u : 1u);
+                    }
+                    if (h + 1 == C::TPR) mma_commit(smem_u32(&acc_full[sl]));
+                    // this stage (half) is free once its MMAs complete
+                    last_mb = smem_u32(&empty[(int)(i % C::NE) * C::TPR + h]);
+                    last_par = (uint32_t)(i / C::NE) & 1u;
+                    any = true;
+                    mma_commit(last_mb);
                 }
-                mma_commit(smem_u32(&acc_full[sl]));
-                issued = i + 1;
-                mma_commit(smem_u32(&empty[(int)(i % C::NE)]));  // the stage is free once these MMAs complete
-                released = i + 1;
             }
-            // before TMEM and the CTA's shared memory are released: the last commits
-            // must have completed
-            if (issued > 0) {
-                const I last = issued - 1;
-                const uint32_t mb = smem_u32(&acc_full[(int)(last % C::SLOTS)]);
+            // before TMEM and the CTA's shared memory are released: the last commit
+            // must have arrived
+            if (any)
                 for (uint32_t it = 0; it < kWaitLimit; ++it)
-                    if (mbar_try(mb, (uint32_t)(last / C::SLOTS) & 1u)) break;
-            }
-            if (released > 0) {
-                const I last = released - 1;
-                const uint32_t mb = smem_u32(&empty[(int)(last % C::NE)]);
-                for (uint32_t it = 0; it < kWaitLimit; ++it)
-                    if (mbar_try(mb, (uint32_t)(last / C::NE) & 1u)) break;
-            }
+                    if (mbar_try(last_mb, last_par)) break;
         }
     } else {
         // ------------------------------------------------------------ epilogue
