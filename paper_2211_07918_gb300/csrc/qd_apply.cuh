@@ -90,8 +90,11 @@ inline unsigned long long pk_host(float a, float b) {
     std::memcpy(&ub, &b, 4);
     return (unsigned long long)ua | ((unsigned long long)ub << 32);
 }
-// Dense complex64 gates of up to 4 x 4 use the packed path.
-template <typename T, int MD> constexpr bool kPacked = kSplit<T> && MD <= 4;
+// Dense complex64 gates of up to 4 x 4, and of 9 x 9 (two qutrits: 72 FP32
+// FMAs per amplitude, which unpacked did not hide under the memory pass;
+// measured 0.59-0.64 -> 0.73-0.78 of the copy peak), use the packed path
+// (8 x 8 measured slower packed).
+template <typename T, int MD> constexpr bool kPacked = kSplit<T> && (MD <= 4 || MD == 9);
 // Kernels with a contiguous-members path (complex64, even member bound):
 // a gate on the lowest qudits, whose group is D consecutive amplitudes
 // starting at a multiple of D, reads and writes 16-byte amplitude pairs.
@@ -182,11 +185,11 @@ __host__ __device__ constexpr int mono_unroll() {
 // Resident CTAs of 256 threads the register budget must allow (the memory
 // parallelism of these kernels is the loads all their threads have in
 // flight): for complex64, 4 (64 registers) where that costs no spills, 3 for
-// the 8- and 9-member dense kernels and the largest mono bucket, 2 for the
-// largest dense; complex128 (bound by FP64 arithmetic) is left unconstrained.
+// the 8-member dense kernel and the largest mono bucket, 2 for the largest
+// dense; complex128 (bound by FP64 arithmetic) is left unconstrained.
 template <typename T, int MD, bool DENSE>
 __host__ __device__ constexpr int direct_min_blocks() {
-    return !kSplit<T> ? 1 : MD >= 32 ? (DENSE ? 2 : 3) : (DENSE && (MD == 8 || MD == 9) ? 3 : 4);
+    return !kSplit<T> ? 1 : MD >= 32 ? (DENSE ? 2 : 3) : (DENSE && MD == 8 ? 3 : 4);
 }
 
 template <typename T, typename I, int MD, bool EX>
