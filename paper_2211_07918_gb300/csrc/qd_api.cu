@@ -133,6 +133,14 @@ int reg_ok(const qd_reg *r) {
     return QD_OK;
 }
 
+// Every qudit dimension a power of two (so every stride and every divisor a
+// gate's kernel takes is one).
+bool all_pow2(const qd_reg *r) {
+    for (int q = 0; q < r->n; ++q)
+        if (r->dims[q] & (r->dims[q] - 1)) return false;
+    return true;
+}
+
 cudaError_t launch_plan(const qd_reg *r, const GatePlan &g) {
     if (g.mode == Mode::Tensor) return launch_block_tc(g, r->psi, r->sm_count, r->dev_err, r->stream);
     if (g.mode == Mode::Table)
@@ -286,6 +294,7 @@ int plan_gate(const qd_reg *r, const double *M, const Acting &a, bool diag_only,
     g.D = D;
     g.N = (uint64_t)r->N;
     g.wide = r->index64 != 0;
+    g.pow2 = all_pow2(r);
     // matrix / classification
     if (force_dense) {  // the dense kernels, whatever the matrix (a dense part with a table epilogue)
         g.kind = Kind::Dense;
@@ -947,6 +956,7 @@ int plan_block_tc(const qd_reg *r, const FuseBlock &b, GatePlan &g, std::vector<
     g.Dp = tc_padded_dim(b.D);
     g.N = (uint64_t)r->N;
     g.wide = r->index64 != 0;
+    g.pow2 = all_pow2(r);
     g.R = (uint64_t)(r->N / b.D);
     std::vector<int> asc(b.qudits.rbegin(), b.qudits.rend());
     std::vector<std::pair<int64_t, int64_t>> ins;
@@ -994,6 +1004,7 @@ int plan_diag_run(const qd_reg *r, const std::vector<FuseGate> &fg, int first, i
     g.kind = Kind::Mono;
     g.N = (uint64_t)r->N;
     g.wide = r->index64 != 0;
+    g.pow2 = all_pow2(r);
     g.tab_div = (uint64_t)r->s[qa];
     uint64_t TS = 1;
     spec.range.nr = qb - qa + 1;

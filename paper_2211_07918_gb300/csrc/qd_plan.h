@@ -29,6 +29,7 @@ struct GatePlan {
     int32_t D = 0;
     uint64_t N = 0;  // register size (selects 32- or 64-bit index arithmetic)
     bool wide = false;  // 64-bit index arithmetic below 2^31 too (QD_TUNE_INDEX64)
+    bool pow2 = false;  // every qudit dimension of the register is a power of two
 
     // --- direct mode: one thread per group --------------------------------
     uint64_t R = 0;          // number of groups
@@ -72,8 +73,15 @@ struct GatePlan {
 };
 
 // 64-bit index kernels: registers of 2^31 amplitudes or more (FastDiv32's
-// dividend bound), or any register when asked for.
-inline bool wide_index(const GatePlan &g) { return g.wide || g.N >= (uint64_t(1) << 31); }
+// dividend bound), or any register when asked for.  A register whose
+// dimensions are all powers of two keeps 32-bit indices up to 2^32
+// amplitudes: every index is below 2^32, and FastDiv32 by a power of two
+// (m = 2^31, a shift of n * 2^31 < 2^63) is exact for every 32-bit n.
+inline bool wide_index(const GatePlan &g) {
+    if (g.wide) return true;
+    if (g.N < (uint64_t(1) << 31)) return false;
+    return !(g.pow2 && g.N <= (uint64_t(1) << 32));
+}
 
 // Per-precision launchers (qd_apply_f32.cu / qd_apply_f64.cu).
 cudaError_t launch_gate_f32(const GatePlan &g, void *psi, int sm_count, cudaStream_t s);

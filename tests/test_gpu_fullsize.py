@@ -120,12 +120,15 @@ def _amplitude(i, dims, factors, states):
     return amp
 
 
+@pytest.mark.parametrize("index64", [False, True])
 @pytest.mark.parametrize("plan_kind", [L.QD_PLAN_NONE, L.QD_PLAN_GREEDY])
-def test_sampled_amplitudes_2_32_vs_oracle(plan_kind):
-    """64-bit index path (2^32 amplitudes, the QFT + ladder register) against
-    the oracle on 4,096 sampled amplitudes of a product-of-factors state:
-    the estimated squared error norm N * mean |psi_i - ref_i|^2 stays within
-    the complex64 fidelity bar (1e-6)."""
+def test_sampled_amplitudes_2_32_vs_oracle(plan_kind, index64):
+    """2^32 amplitudes (the QFT + ladder register: every dimension a power of
+    two, so the gate kernels keep 32-bit indices up to 2^32 - 1; index64
+    forces the 64-bit kernels) against the oracle on 4,096 sampled
+    amplitudes of a product-of-factors state: the estimated squared error
+    norm N * mean |psi_i - ref_i|^2 stays within the complex64 fidelity bar
+    (1e-6)."""
     torch = pytest.importorskip("torch")
     dims, _ = wl.circuit_c2()
     N = int(np.prod(dims))
@@ -135,6 +138,8 @@ def test_sampled_amplitudes_2_32_vs_oracle(plan_kind):
     buf = torch.zeros(N, dtype=torch.complex64, device="cuda")
     h = L.qd_create(dims, None, L.QD_C64, buf.data_ptr(), buf.numel() * 8, 0)
     try:
+        if index64:
+            L.qd_set_tuning(h, L.QD_TUNE_INDEX64, 1)
         plan = L.qd_plan_create(h, gates, plan_kind)
         L.qd_plan_run(plan)
         assert L.qd_sync(h) == 0
