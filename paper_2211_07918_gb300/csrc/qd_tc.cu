@@ -40,12 +40,16 @@
 //
 // Warp roles (the steps of a tile overlap across tiles):
 //   producers (8 warps: two groups of 128 rows alternating tiles, or above
-//     D = 32 one group with two threads per row): gather a tile's groups,
-//     slice them in registers, then (once the stage is free) store the
-//     slices into stage s of a shared-memory ring and arrive full[s];
+//     D = 32 one group whose warps 5..8 hold amplitudes 0..31 of every row
+//     and warps 9..12 the rest): gather a tile's groups, slice them in
+//     registers, then (once the stage is free) store the slices into stage s
+//     of a shared-memory ring and arrive full[s]; above D = 32 each set of
+//     warps writes its own K half of the single stage, waiting on that
+//     half's empty barrier and arriving on its full barrier;
 //   MMA issuer (warp 4, one lane): wait full[s] and acc_empty[a], issue the
-//     slice products into accumulator slot a of a 2-slot TMEM ring, commit to
-//     acc_full[a];
+//     slice products into accumulator slot a of a 2-slot TMEM ring (above
+//     D = 32 one K half at a time, each half's stage released by its own
+//     commit), commit to acc_full[a];
 //   epilogue (warps 0..3, one TMEM lane per thread): wait acc_full[a], add the
 //     two accumulators, scatter the outputs, arrive acc_empty[a].
 // A stage is released by a tcgen05.commit to empty[s] once its MMAs have
