@@ -730,6 +730,46 @@ cudaError_t launch_dense(const GatePlan &g, void *psi, int sm_count, cudaStream_
     return cudaGetLastError();
 }
 
+// A permutation with phases whose moved members are few (a fused Toffoli
+// rung moves 2 of its 16): only the active members enter the kernel, as a
+// list of at most MD, so the kernel of that bound runs with its groups per
+// thread (4 for two members): more loads in flight for the same groups.
+template <typename T, typename I, int MD>
+cudaError_t launch_mono_compact(const GatePlan &g, void *psi, int sm_count, cudaStream_t s) {
+    MonoDirectArgs<T, I, MD> a;
+    a.psi = static_cast<v2<T> *>(psi);
+    a.R = (I)g.R;
+    a.base = (I)g.base_off;
+    a.ex = expand_for<I>(g.ex);
+    int na = 0;
+    uint32_t unit = 0;
+    for (int i = 0; i < g.D && na < MD; ++i) {
+        if (!((g.active >> i) & 1u)) continue;
+        a.off[na] = (I)g.off[i];
+        a.offsrc[na] = (I)g.off[g.src[i]];
+        v2<T> hi, lo;
+        split_coef<T>(g.lam[2 * i], g.lam[2 * i + 1], hi, lo);
+        a.lam[na] = hi;
+        if constexpr (kSplit<T>) a.lamlo[na] = lo;
+        if ((g.unit >> i) & 1u) unit |= 1u << na;
+        ++na;
+    }
+    for (int k = na; k < MD; ++k) {
+        a.off[k] = 0;
+        a.offsrc[k] = 0;
+        a.lam[k] = mk<T>(T(1), T(0));
+        if constexpr (kSplit<T>) a.lamlo[k] = mk<T>(T(0), T(0));
+    }
+    if constexpr (!kSplit<T>) a.lamlo[0] = mk<T>(T(0), T(0));
+    a.active = (1u << na) - 1u;
+    a.unit = unit;
+    auto fn = k_mono_direct<T, I, MD>;
+    const int grid = grid_of(g.R, kBlock, sm_count, occupancy_blocks((const void *)fn, kBlock, 0));
+    if (grid <= 0) return cudaSuccess;
+    fn<<<grid, kBlock, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 template <typename T, typename I, int MD>
 cudaError_t launch_mono(const GatePlan &g, void *psi, int sm_count, cudaStream_t s) {
     if (g.mode == Mode::Direct) {
@@ -822,6 +862,11 @@ cudaError_t launch_gate_ti(const GatePlan &g, void *psi, int sm_count, cudaStrea
         return launch_dense_table<T, I, 16, false>(g, psi, sm_count, s);
     }
     if (g.kind == Kind::Mono) {
+        if (g.mode == Mode::Direct && g.D > 4) {
+            const int na = __builtin_popcount(g.active & (g.D >= 32 ? 0xffffffffu : ((1u << g.D) - 1u)));
+            if (na <= 2) return launch_mono_compact<T, I, 2>(g, psi, sm_count, s);
+            if (na <= 4) return launch_mono_compact<T, I, 4>(g, psi, sm_count, s);
+        }
         if (g.D <= 2) return launch_mono<T, I, 2>(g, psi, sm_count, s);
         if (g.D <= 4) return launch_mono<T, I, 4>(g, psi, sm_count, s);
         if (g.D <= 8) return launch_mono<T, I, 8>(g, psi, sm_count, s);
