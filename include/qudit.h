@@ -142,10 +142,11 @@ int qd_set_stream(qd_reg *reg, void *stream);
 #define QD_TUNE_FUSE_KMAX 2
 #define QD_TUNE_FUSE_DMAX 3
 #define QD_TUNE_TC_MIN_D 4
-/* QD_TUNE_INDEX64: 1 runs the 64-bit index kernels (taken by every register
- * of 2^31 amplitudes or more) on this register whatever its size, for plans
- * created afterwards and for one-shot gate calls; 0 (default) lets the size
- * decide. */
+/* QD_TUNE_INDEX64: 1 runs the 64-bit index kernels on this register
+ * whatever its size (by default they run on registers of 2^31 amplitudes
+ * or more, except registers of up to 2^32 whose dimensions are all powers
+ * of two, which keep 32-bit indices), for plans created afterwards and for
+ * one-shot gate calls; 0 (default) lets the size decide. */
 #define QD_TUNE_INDEX64 5
 int qd_set_tuning(qd_reg *reg, int32_t key, int64_t value);
 
