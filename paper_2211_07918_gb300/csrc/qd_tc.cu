@@ -39,17 +39,17 @@
 // (leading byte offset), 8-row groups at K*16 B (stride byte offset).
 //
 // Warp roles (the steps of a tile overlap across tiles):
-//   producers (8 warps: two groups of 128 rows alternating tiles, or above
-//     D = 32 one group whose warps 5..8 hold amplitudes 0..31 of every row
-//     and warps 9..12 the rest): gather a tile's groups, slice them in
-//     registers, then (once the stage is free) store the slices into stage s
-//     of a shared-memory ring and arrive full[s]; above D = 32 each set of
-//     warps writes its own K half of the single stage, waiting on that
-//     half's empty barrier and arriving on its full barrier;
+//   producers (8 warps: two groups of 128 rows alternating tiles; above
+//     D = 32, 16 warps in four parts of four warps, part p holding
+//     amplitudes 16p..16p+15 of every row): gather a tile's groups, slice
+//     them in registers, then (once the stage is free) store the slices into
+//     stage s of a shared-memory ring and arrive full[s]; above D = 32 each
+//     part writes its own K quarter of the single stage, waiting on that
+//     quarter's empty barrier and arriving on its full barrier;
 //   MMA issuer (warp 4, one lane): wait full[s] and acc_empty[a], issue the
 //     slice products into accumulator slot a of a 2-slot TMEM ring (above
-//     D = 32 one K half at a time, each half's stage released by its own
-//     commit), commit to acc_full[a];
+//     D = 32 one K quarter at a time, each quarter of the stage released by
+//     its own commit), commit to acc_full[a];
 //   epilogue (warps 0..3, one TMEM lane per thread): wait acc_full[a], add the
 //     two accumulators, scatter the outputs, arrive acc_empty[a].
 // A stage is released by a tcgen05.commit to empty[s] once its MMAs have
@@ -168,19 +168,19 @@ template <int MAXD> struct TcCfg {
     static constexpr int NACC = 2;    // accumulators per slot: exact leading level, corrections
     static constexpr int SLOTS = 2;   // TMEM accumulator ring (2 x 2 x 2 Dp <= 512 columns)
     static constexpr int STAGES = MAXD <= 32 ? 3 : 1;   // shared-memory ring
-    static constexpr int PW = 8;                        // producer warps
-    // threads per tile row: above 32 amplitudes two threads share a row (32
-    // amplitudes each), so that 8 producer warps fit the registers
-    static constexpr int TPR = MAXD <= 32 ? 1 : 2;
+    static constexpr int PW = MAXD <= 32 ? 8 : 16;      // producer warps
+    // threads per tile row: above 32 amplitudes four threads share a row (16
+    // amplitudes each: 21 warps of at most 96 registers)
+    static constexpr int TPR = MAXD <= 32 ? 1 : 4;
     static constexpr int NGRP = PW * 32 / (kTcRows * TPR);  // producer groups (alternate tiles)
     static constexpr int RA = MAXD / TPR;                   // amplitudes per producer thread
     static constexpr int THREADS = 32 * (5 + PW);
     static constexpr int NPAIRS = 6;
     static constexpr bool PRE = MAXD <= 32;  // slices built before the stage is free
-    // Above D = 32 the single stage is written in two K halves, each by the
-    // threads that hold its amplitudes (part 0: amplitudes 0..31, part 1:
-    // the rest) and released by the MMAs of that half alone: while one half's
-    // MMAs run, the other half of the next tile is sliced and stored.
+    // Above D = 32 the single stage is written in four K quarters, each by
+    // the threads that hold its amplitudes and released by the MMAs of that
+    // quarter alone: while some quarters' MMAs run, the other quarters of the
+    // next tile are sliced and stored.
     // Stage-release barriers: tile i's MMAs commit to empty[i % NE]; the
     // writer of tile i waits for tile i - STAGES on empty[(i - STAGES) % NE].
     // With one stage NE = 2 (one barrier per tile parity): should two
@@ -262,13 +262,13 @@ __global__ void __launch_bounds__(TcCfg<MAXD>::THREADS, 1) k_block_tc(const __gr
     const float *bscale = reinterpret_cast<const float *>(B + 3u * bbytes);
     const uint32_t bregion = (3u * bbytes + K * 4u + 1023u) & ~1023u;
     unsigned char *stages = sm + bregion;  // stage s: X1 | X2 | X3 at s * XS * xbytes
-    // full / empty: one barrier per stage (and K half, above D = 32)
+    // full / empty: one barrier per stage (and K quarter, above D = 32)
     __shared__ __align__(8) uint64_t full[C::STAGES * C::TPR], empty[C::NE * C::TPR], acc_full[C::SLOTS],
         acc_empty[C::SLOTS];
-    // above D = 32: the two halves of a row exchange their maxima through
+    // above D = 32: the four parts of a row exchange their maxima through
     // shared memory (a 2-deep ring, one barrier per slot)
     __shared__ __align__(8) uint64_t xm_full[2];
-    __shared__ float xmax[2][2][kTcRows];
+    __shared__ float xmax[2][C::TPR][kTcRows];
     // row scales of a tile: a 2-deep ring between producers and epilogue
     __shared__ __align__(8) uint64_t sc_full[2], sc_empty[2];
     __shared__ int32_t erow[2][kTcRows];
@@ -294,7 +294,7 @@ __global__ void __launch_bounds__(TcCfg<MAXD>::THREADS, 1) k_block_tc(const __gr
         for (int q = 0; q < C::NE * C::TPR; ++q)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&empty[q])) : "memory");
         for (int q = 0; q < 2; ++q)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&xm_full[q])), "r"(2 * kTcRows)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&xm_full[q])), "r"(C::TPR * kTcRows)
                          : "memory");
         for (int q = 0; q < C::SLOTS; ++q) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&acc_full[q])) : "memory");
@@ -359,7 +359,7 @@ __global__ void __launch_bounds__(TcCfg<MAXD>::THREADS, 1) k_block_tc(const __gr
             float amax = 0.f;
 #pragma unroll
             for (int j = 0; j < C::RA; ++j) amax = fmaxf(amax, fmaxf(fabsf(v[j].x), fabsf(v[j].y)));
-            if constexpr (C::TPR == 2) {
+            if constexpr (C::TPR > 1) {
                 const int xs = (int)(i & 1);
                 xmax[xs][part][row] = amax;
                 mbar_arrive(smem_u32(&xm_full[xs]));
@@ -368,7 +368,9 @@ __global__ void __launch_bounds__(TcCfg<MAXD>::THREADS, 1) k_block_tc(const __gr
                 bool okx = ws_wait(smem_u32(&xm_full[xs]), (uint32_t)(i >> 1) & 1u, &abort_flag, a.err);
                 okx = __all_sync(0xffffffffu, okx);
                 if (!okx) break;
-                amax = fmaxf(xmax[xs][0][row], xmax[xs][1][row]);
+                amax = xmax[xs][0][row];
+#pragma unroll
+                for (int pp = 1; pp < C::TPR; ++pp) amax = fmaxf(amax, xmax[xs][pp][row]);
             }
             int e = 0;
             frexpf(amax, &e);  // amax <= 2^e
@@ -392,10 +394,10 @@ __global__ void __launch_bounds__(TcCfg<MAXD>::THREADS, 1) k_block_tc(const __gr
             {
                 const int es = (int)(i & 1);
                 const uint32_t euse = (uint32_t)(i >> 1);
-                // with two threads per row the warp leaves the loop together (the
-                // row maximum is exchanged by shuffles): every lane reaches the vote
+                // with several threads per row the warp leaves the loop together
+                // (every lane takes the same exits): every lane reaches the vote
                 bool ok = euse < 1 || ws_wait(smem_u32(&sc_empty[es]), (euse - 1) & 1u, &abort_flag, a.err);
-                if constexpr (C::TPR == 2) ok = __all_sync(0xffffffffu, ok);
+                if constexpr (C::TPR > 1) ok = __all_sync(0xffffffffu, ok);
                 if (!ok) break;
                 if (part == 0) {
                     erow[es][row] = e;
@@ -408,7 +410,7 @@ __global__ void __launch_bounds__(TcCfg<MAXD>::THREADS, 1) k_block_tc(const __gr
                 ok = ws_wait(smem_u32(&empty[(int)(wt % C::NE) * C::TPR + part]), (uint32_t)(wt / C::NE) & 1u,
                              &abort_flag, a.err);
             }
-            if constexpr (C::TPR == 2) ok = __all_sync(0xffffffffu, ok);
+            if constexpr (C::TPR > 1) ok = __all_sync(0xffffffffu, ok);
             if (!ok) break;
             unsigned char *X = stages + (uint32_t)st * C::XS * xbytes;
 #pragma unroll
@@ -449,7 +451,9 @@ __global__ void __launch_bounds__(TcCfg<MAXD>::THREADS, 1) k_block_tc(const __gr
             const int pairs[6][3] = {{0, 0, 0}, {1, 0, 1}, {1, 1, 0}, {1, 0, 2}, {1, 1, 1}, {1, 2, 0}};
             const uint32_t ksteps = K / 16u;
             // K steps of the first half: the columns of part 0's amplitudes
-            const uint32_t khalf = C::TPR == 2 ? std::min<uint32_t>(ksteps, (uint32_t)(2 * C::RA / 16)) : ksteps;
+            // K steps of each part's columns (2 RA of them): part h writes and
+            // releases K steps [h kpart, (h + 1) kpart) of the stage
+            const uint32_t kpart = (uint32_t)(2 * C::RA / 16);
             // the most recent commit: once it has arrived, every MMA issued
             // before it has completed
             uint32_t last_mb = 0, last_par = 0;
@@ -471,10 +475,11 @@ __global__ void __launch_bounds__(TcCfg<MAXD>::THREADS, 1) k_block_tc(const __gr
                 // (shared addresses stay below 2^18, so the field does not overflow)
 #pragma unroll
                 for (int h = 0; h < C::TPR; ++h) {
-                    const uint32_t k_lo = h == 0 ? 0u : khalf, k_hi = h == 0 ? khalf : ksteps;
-                    if (h == 1) {
-                        // the second half of the stage, written by part 1
-                        if (!ws_wait(smem_u32(&full[st * C::TPR + 1]), fpar, &abort_flag, a.err)) {
+                    const uint32_t k_lo = std::min<uint32_t>((uint32_t)h * kpart, ksteps);
+                    const uint32_t k_hi = h + 1 == C::TPR ? ksteps : std::min<uint32_t>((uint32_t)(h + 1) * kpart, ksteps);
+                    if (h > 0) {
+                        // the next part of the stage, written by its own producer warps
+                        if (!ws_wait(smem_u32(&full[st * C::TPR + h]), fpar, &abort_flag, a.err)) {
                             good = false;
                             break;
                         }
