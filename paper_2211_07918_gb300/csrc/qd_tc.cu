@@ -39,17 +39,16 @@
 // (leading byte offset), 8-row groups at K*16 B (stride byte offset).
 //
 // Warp roles (the steps of a tile overlap across tiles):
-//   producers (8 warps: two groups of 128 rows alternating tiles; above
-//     D = 32, 16 warps in four parts of four warps, part p holding
-//     amplitudes 16p..16p+15 of every row): gather a tile's groups, slice
-//     them in registers, then (once the stage is free) store the slices into
-//     stage s of a shared-memory ring and arrive full[s]; above D = 32 each
-//     part writes its own K quarter of the single stage, waiting on that
-//     quarter's empty barrier and arriving on its full barrier;
-//   MMA issuer (warp 4, one lane): wait full[s] and acc_empty[a], issue the
-//     slice products into accumulator slot a of a 2-slot TMEM ring (above
-//     D = 32 one K quarter at a time, each quarter of the stage released by
-//     its own commit), commit to acc_full[a];
+//   producers (up to D = 32, 8 warps in two groups alternating tiles, one
+//     thread per row; above D = 32, 16 warps in one group of four parts;
+//     part p holds amplitudes p RA .. (p + 1) RA - 1 of every row):
+//     gather a tile's groups, slice them in registers, then (once its part
+//     of the stage is free) store the slices of its K part into stage s of
+//     a shared-memory ring and arrive full[s][p];
+//   MMA issuer (warp 4, one lane): wait full[s][p] and acc_empty[a], issue
+//     the slice products into accumulator slot a of a 2-slot TMEM ring one K
+//     part at a time, each part of the stage released by its own commit to
+//     empty[s][p], and commit to acc_full[a];
 //   epilogue (warps 0..3, one TMEM lane per thread): wait acc_full[a], add the
 //     two accumulators, scatter the outputs, arrive acc_empty[a].
 // A stage is released by a tcgen05.commit to empty[s] once its MMAs have
@@ -169,18 +168,21 @@ template <int MAXD> struct TcCfg {
     static constexpr int SLOTS = 2;   // TMEM accumulator ring (2 x 2 x 2 Dp <= 512 columns)
     static constexpr int STAGES = MAXD <= 32 ? 3 : 1;   // shared-memory ring
     static constexpr int PW = MAXD <= 32 ? 8 : 16;      // producer warps
-    // threads per tile row: above 32 amplitudes four threads share a row (16
-    // amplitudes each: 21 warps of at most 96 registers)
+    // threads per tile row (the parts of a row, each holding RA amplitudes
+    // and writing its own K part of the stage): one up to D = 32 (two
+    // producer groups of 4 warps alternate tiles over three stages; two
+    // parts of a row measured slower there), four above (21 warps of at most
+    // 96 registers: 0.575 -> 0.727 of the copy peak at D = 64)
     static constexpr int TPR = MAXD <= 32 ? 1 : 4;
     static constexpr int NGRP = PW * 32 / (kTcRows * TPR);  // producer groups (alternate tiles)
     static constexpr int RA = MAXD / TPR;                   // amplitudes per producer thread
     static constexpr int THREADS = 32 * (5 + PW);
     static constexpr int NPAIRS = 6;
     static constexpr bool PRE = MAXD <= 32;  // slices built before the stage is free
-    // Above D = 32 the single stage is written in four K quarters, each by
-    // the threads that hold its amplitudes and released by the MMAs of that
-    // quarter alone: while some quarters' MMAs run, the other quarters of the
-    // next tile are sliced and stored.
+    // A stage is written in TPR K parts, each by the threads that hold its
+    // amplitudes and released by the MMAs of that part alone: while some
+    // parts' MMAs run, the other parts of the next tile are sliced and
+    // stored (with one stage above D = 32, this is the only overlap).
     // Stage-release barriers: tile i's MMAs commit to empty[i % NE]; the
     // writer of tile i waits for tile i - STAGES on empty[(i - STAGES) % NE].
     // With one stage NE = 2 (one barrier per tile parity): should two
@@ -262,13 +264,14 @@ __global__ void __launch_bounds__(TcCfg<MAXD>::THREADS, 1) k_block_tc(const __gr
     const float *bscale = reinterpret_cast<const float *>(B + 3u * bbytes);
     const uint32_t bregion = (3u * bbytes + K * 4u + 1023u) & ~1023u;
     unsigned char *stages = sm + bregion;  // stage s: X1 | X2 | X3 at s * XS * xbytes
-    // full / empty: one barrier per stage (and K quarter, above D = 32)
+    // full / empty: one barrier per stage and K part
     __shared__ __align__(8) uint64_t full[C::STAGES * C::TPR], empty[C::NE * C::TPR], acc_full[C::SLOTS],
         acc_empty[C::SLOTS];
-    // above D = 32: the four parts of a row exchange their maxima through
+    // the parts of a row exchange their maxima through
     // shared memory (a 2-deep ring, one barrier per slot)
-    __shared__ __align__(8) uint64_t xm_full[2];
-    __shared__ float xmax[2][C::TPR][kTcRows];
+    // (a 2-deep ring per producer group: slot 2 grp + (local tile & 1))
+    __shared__ __align__(8) uint64_t xm_full[2 * C::NGRP];
+    __shared__ float xmax[2 * C::NGRP][C::TPR][kTcRows];
     // row scales of a tile: a 2-deep ring between producers and epilogue
     __shared__ __align__(8) uint64_t sc_full[2], sc_empty[2];
     __shared__ int32_t erow[2][kTcRows];
@@ -293,7 +296,7 @@ __global__ void __launch_bounds__(TcCfg<MAXD>::THREADS, 1) k_block_tc(const __gr
         // a stage (half) is free once the MMAs reading it have completed (tcgen05.commit)
         for (int q = 0; q < C::NE * C::TPR; ++q)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&empty[q])) : "memory");
-        for (int q = 0; q < 2; ++q)
+        for (int q = 0; q < 2 * C::NGRP; ++q)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&xm_full[q])), "r"(C::TPR * kTcRows)
                          : "memory");
         for (int q = 0; q < C::SLOTS; ++q) {
@@ -360,12 +363,15 @@ __global__ void __launch_bounds__(TcCfg<MAXD>::THREADS, 1) k_block_tc(const __gr
 #pragma unroll
             for (int j = 0; j < C::RA; ++j) amax = fmaxf(amax, fmaxf(fabsf(v[j].x), fabsf(v[j].y)));
             if constexpr (C::TPR > 1) {
-                const int xs = (int)(i & 1);
+                // the group's local tile li: slot 2 grp + (li & 1), phase li >> 1.
+                // A slot is rewritten two of the group's tiles later, after every
+                // thread of the group has passed the exchange in between (and so
+                // has read this one)
+                const I li = i / (I)NGRP;
+                const int xs = 2 * grp + (int)(li & 1);
                 xmax[xs][part][row] = amax;
                 mbar_arrive(smem_u32(&xm_full[xs]));
-                // a slot is rewritten two tiles later, after every thread has
-                // passed the next exchange (and so has read this one)
-                bool okx = ws_wait(smem_u32(&xm_full[xs]), (uint32_t)(i >> 1) & 1u, &abort_flag, a.err);
+                bool okx = ws_wait(smem_u32(&xm_full[xs]), (uint32_t)(li >> 1) & 1u, &abort_flag, a.err);
                 okx = __all_sync(0xffffffffu, okx);
                 if (!okx) break;
                 amax = xmax[xs][0][row];
