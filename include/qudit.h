@@ -455,7 +455,7 @@ int qd_segment_features(qd_reg *reg, const qd_gate *gates, int32_t ngates, int32
  * qd_plan_create_segmented (the candidates a planner weighs): *nforms of
  * them (at most 3), kinds[i] the kernel form (QD_FORM_*) and features[i*12..] its 12
  * launch features, for i < cap.  QD_ERR_OOM when *nforms > cap (the first
- * cap are written). */
+ * cap are written), except for a count query (cap 0, both arrays NULL). */
 int qd_segment_forms(qd_reg *reg, const qd_gate *gates, int32_t ngates, int32_t first, int32_t last, int32_t *kinds,
                      float *features, int32_t cap, int32_t *nforms);
 /* A plan from an explicit segmentation: segment i covers the non-identity

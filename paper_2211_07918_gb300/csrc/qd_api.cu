@@ -1354,6 +1354,7 @@ int qd_segment_forms(qd_reg *r, const qd_gate *gates, int32_t ngates, int32_t fi
         kinds[i] = (int32_t)forms[i].f[10];
         std::copy(forms[i].f, forms[i].f + kFeatures, features + (size_t)i * kFeatures);
     }
+    if (cap == 0 && !kinds && !features) return QD_OK;  // a count query
     return (int)forms.size() > cap ? fail(QD_ERR_OOM, "more forms than the arrays hold") : QD_OK;
 }
 

@@ -357,6 +357,13 @@ def test_every_kernel_form_of_a_segment(prec):
         assert kinds == want, kinds
         feat = L.qd_segment_features(r.h, gates, 0, len(gates) - 1)
         assert int(feat[10]) in kinds
+        # a count query (no arrays)
+        import ctypes
+        n = ctypes.c_int32(-1)
+        ga = L.GateArray(gates)
+        assert L.load().qd_segment_forms(ctypes.c_void_p(r.h), ga.ptr, ga.n, 0, len(gates) - 1, None, None, 0,
+                                         ctypes.byref(n)) == 0
+        assert n.value == len(forms)
         for k, f in forms:
             assert int(f[10]) == k
             L.qd_set_amplitudes(r.h, psi0)
