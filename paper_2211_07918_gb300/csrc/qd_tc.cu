@@ -175,6 +175,9 @@ template <int MAXD> struct TcCfg {
     // 96 registers: 0.575 -> 0.727 of the copy peak at D = 64)
     static constexpr int TPR = MAXD <= 32 ? 1 : 4;
     static constexpr int NGRP = PW * 32 / (kTcRows * TPR);  // producer groups (alternate tiles)
+    // the row-scale ring's slot is tile & 1: with more than two groups two of
+    // them would share a slot and wait on phases two apart (parity aliasing)
+    static_assert(NGRP >= 1 && NGRP <= 2, "at most two producer groups");
     static constexpr int RA = MAXD / TPR;                   // amplitudes per producer thread
     static constexpr int THREADS = 32 * (5 + PW);
     static constexpr int NPAIRS = 6;
