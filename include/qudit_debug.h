@@ -41,6 +41,12 @@ int qd_debug_fuse_plan(const int32_t *dims, int32_t n, int32_t precision, const 
  * gates (one gate: its own kernel; several: one dense block). */
 int qd_debug_segment_cost(const int32_t *dims, int32_t n, int32_t precision, const qd_gate *gates, int32_t ngates,
                           int32_t first, int32_t last, double *cost);
+/* The feasible kernel forms of the segment [first, last] (as
+ * qd_segment_forms, for a register of dims[0..n) at `precision`, no device):
+ * *nforms of them, kinds[i] (QD_FORM_*) and features[i*12..] for i < cap. */
+int qd_debug_segment_forms(const int32_t *dims, int32_t n, int32_t precision, const qd_gate *gates, int32_t ngates,
+                           int32_t first, int32_t last, int32_t *kinds, float *features, int32_t cap,
+                           int32_t *nforms);
 /* The fused block of gates [first, last]: its qudits (first = most
  * significant local digit, at most 6) and its D x D FP64 matrix (interleaved
  * complex, row-major; cap doubles available). */

@@ -1841,6 +1841,25 @@ int qd_debug_segment_cost(const int32_t *dims, int32_t n, int32_t precision, con
     return QD_OK;
 }
 
+int qd_debug_segment_forms(const int32_t *dims, int32_t n, int32_t precision, const qd_gate *gates, int32_t ngates,
+                           int32_t first, int32_t last, int32_t *kinds, float *features, int32_t cap,
+                           int32_t *nforms) {
+    qd_reg r;
+    if (int rc = host_register(dims, n, precision, r)) return rc;
+    if (!nforms || cap < 0 || (cap > 0 && (!kinds || !features))) return fail(QD_ERR_ARG, "bad output arrays");
+    std::vector<FuseGate> fg;
+    std::vector<const qd_gate *> orig;
+    if (int rc = collect_gates(&r, gates, ngates, fg, orig)) return rc;
+    if (first < 0 || last < first || last >= (int)fg.size()) return fail(QD_ERR_ARG, "bad segment");
+    const std::vector<LaunchFeatures> forms = segment_forms(fg, first, last, hard_shape(&r), QD_MAX_TARGETS);
+    *nforms = (int32_t)forms.size();
+    for (int i = 0; i < (int)forms.size() && i < cap; ++i) {
+        kinds[i] = (int32_t)forms[i].f[10];
+        std::copy(forms[i].f, forms[i].f + kFeatures, features + (size_t)i * kFeatures);
+    }
+    return (int)forms.size() > cap ? fail(QD_ERR_OOM, "more forms than the arrays hold") : QD_OK;
+}
+
 int qd_debug_fuse_block(const int32_t *dims, int32_t n, const qd_gate *gates, int32_t ngates, int32_t first,
                         int32_t last, int32_t *qudits, int32_t *k, int32_t *D, double *matrix, int64_t cap) {
     qd_reg r;

@@ -559,6 +559,23 @@ def qd_debug_segment_cost(dims, gates, first, last, precision=QD_C64):
     return c.value
 
 
+def qd_debug_segment_forms(dims, gates, first, last, precision=QD_C64):
+    """[(kernel form, 12 features)] of every feasible form of a segment (host only)."""
+    L = load()
+    fn = L.qd_debug_segment_forms
+    fn.argtypes = [_i32p, _i32, _i32, ctypes.POINTER(QdGate), _i32, _i32, _i32, _i32p,
+                   ctypes.POINTER(ctypes.c_float), _i32, _i32p]
+    fn.restype = ctypes.c_int
+    d, dp = _arr_i32(dims)
+    ga = GateArray(gates)
+    k, kp = _arr_i32([0] * 4)
+    feats = np.zeros((4, QD_MODEL_FEATURES), np.float32)
+    n = _i32(0)
+    _check(fn(dp, len(d), precision, ga.ptr, ga.n, first, last, kp, feats.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+              4, ctypes.byref(n)))
+    return [(int(k[i]), feats[i].copy()) for i in range(n.value)]
+
+
 def qd_debug_fuse_block(dims, gates, first, last):
     """(qudits, D x D complex matrix) of the fused block of gates[first..last]."""
     L = load()

@@ -184,3 +184,45 @@ def test_diagonal_runs_are_planned_as_single_segments():
         assert k < b, (a, b)  # a diagonal suffix
         assert len(pre) <= 3 and int(np.prod([dims[q] for q in pre])) <= 16, (a, b)
     assert wide >= 1
+
+
+def test_segment_forms_enumeration():
+    """The kernel forms a planner weighs for one segment (host replay of
+    qd_segment_forms): a dense gate on qudits (1, 2) followed by diagonal
+    gates on qudits 1..3 is a fused block (CUDA-core kernel; tensor cores
+    too for complex64, D = 18 >= 9) or a dense part + diagonal run; a single
+    gate has its own kernel only; a run of diagonal gates over many qudits is
+    a diagonal run (a mono block too while it fits a block); dense gates
+    with no diagonal tail have no dense part + run form.  Feature 10 names
+    the form, feature 0 is log2 of its dimension (of the table for a run)."""
+    rng = np.random.default_rng(4)
+    dims = [2, 3, 3, 2, 4, 3]
+    seg = [Gate("U", (1, 2), matrix=wl.haar_unitary(9, rng)), Gate("Z", (1,), param=1),
+           Gate("DIAG", (3,), (2,), (2,), matrix=np.exp(2j * np.pi * rng.random(2)))]
+    for prec, want in ((L.QD_C64, [L.QD_FORM_BLOCK, L.QD_FORM_BLOCK_TC, L.QD_FORM_DENSE_RUN]),
+                       (L.QD_C128, [L.QD_FORM_BLOCK, L.QD_FORM_DENSE_RUN])):
+        forms = L.qd_debug_segment_forms(dims, seg, 0, 2, prec)
+        assert sorted(k for k, _ in forms) == want
+        for k, f in forms:
+            assert int(f[10]) == k
+            if k in (L.QD_FORM_BLOCK, L.QD_FORM_BLOCK_TC):
+                assert abs(f[0] - np.log2(18)) < 1e-6 and f[1] == 3  # qudits 1, 2, 3
+            else:
+                assert abs(f[0] - np.log2(9)) < 1e-6 and f[1] == 2  # the dense part on 1, 2
+    # one gate: its own kernel
+    assert [k for k, _ in L.qd_debug_segment_forms(dims, seg[:1], 0, 0)] == [L.QD_FORM_DENSE]
+    assert [k for k, _ in L.qd_debug_segment_forms(dims, seg[1:2], 0, 0)] == [L.QD_FORM_MONO]
+    # two dense gates, no diagonal tail: blocks only
+    two = [Gate("U", (0, 1), matrix=wl.haar_unitary(6, rng)), Gate("U", (1, 4), matrix=wl.haar_unitary(12, rng))]
+    assert sorted(k for k, _ in L.qd_debug_segment_forms(dims, two, 0, 1)) == [L.QD_FORM_BLOCK, L.QD_FORM_BLOCK_TC]
+    # diagonal gates: over qudits 0..2 (18 states) one permutation-with-phases
+    # block; over 0..4 (144 states, beyond the 32 of such a block) one
+    # diagonal run whose table has 144 entries
+    diag = [Gate("DIAG", (q, q + 1), matrix=np.exp(2j * np.pi * rng.random(dims[q] * dims[q + 1])))
+            for q in range(4)]
+    forms = L.qd_debug_segment_forms(dims, diag, 0, 1)
+    assert [k for k, _ in forms] == [L.QD_FORM_MONO]
+    assert abs(forms[0][1][0] - np.log2(18)) < 1e-6 and forms[0][1][1] == 3
+    forms = L.qd_debug_segment_forms(dims, diag, 0, 3)
+    assert [k for k, _ in forms] == [L.QD_FORM_DIAG_RUN]
+    assert abs(forms[0][1][0] - np.log2(144)) < 1e-5 and forms[0][1][1] == 5
